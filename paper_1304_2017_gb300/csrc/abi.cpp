@@ -1,0 +1,144 @@
+// extern "C" entry points declared in include/oat.h: argument checks, device selection,
+// error reporting.  All arithmetic lives in the kernels (forward.cu, adjoint.cu) and the
+// plan builder (plan.cpp).
+#include <cstdint>
+#include <string>
+
+#include "oat_internal.h"
+
+namespace oat {
+
+int plan_create(const oat_geometry *g, int device, Plan **out);
+void plan_destroy(Plan *p);
+
+static thread_local std::string g_last_error;
+
+int set_error(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+namespace {
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Makes the plan's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) err = cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+}  // namespace oat
+
+using namespace oat;
+
+extern "C" {
+
+int oat_version(void) { return 10000; }
+
+const char *oat_last_error(void) { return g_last_error.c_str(); }
+
+int oat_plan_create(const oat_geometry *geom, int device, oat_plan *out) {
+    if (!out) return set_error(OAT_ERR_INVALID_ARG, "oat_plan_create: out is NULL");
+    *out = nullptr;
+    Plan *p = nullptr;
+    int rc = plan_create(geom, device, &p);
+    if (rc != OAT_OK) return rc;
+    *out = reinterpret_cast<oat_plan>(p);
+    g_last_error.clear();
+    return OAT_OK;
+}
+
+int oat_plan_destroy(oat_plan plan) {
+    plan_destroy(reinterpret_cast<Plan *>(plan));
+    return OAT_OK;
+}
+
+int oat_project(oat_plan plan, const float *d_vol, void *d_data, void *stream) {
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || !d_vol || !d_data) return set_error(OAT_ERR_INVALID_ARG, "oat_project: NULL plan or buffer");
+    if (!aligned16(d_vol) || !aligned16(d_data))
+        return set_error(OAT_ERR_INVALID_ARG, "oat_project: buffers must be 16-byte aligned");
+    DeviceGuard dg(p->device);
+    if (dg.err != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_project: ") + cudaGetErrorString(dg.err));
+    return launch_project(*p, d_vol, d_data, (cudaStream_t)stream);
+}
+
+int oat_backproject(oat_plan plan, const void *d_data, float *d_vol, void *stream) {
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || !d_vol || !d_data) return set_error(OAT_ERR_INVALID_ARG, "oat_backproject: NULL plan or buffer");
+    if (!aligned16(d_vol) || !aligned16(d_data))
+        return set_error(OAT_ERR_INVALID_ARG, "oat_backproject: buffers must be 16-byte aligned");
+    DeviceGuard dg(p->device);
+    if (dg.err != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_backproject: ") + cudaGetErrorString(dg.err));
+    return launch_backproject(*p, d_data, d_vol, (cudaStream_t)stream);
+}
+
+int oat_plan_query(oat_plan plan, int want_count, oat_stats *st) {
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || !st) return set_error(OAT_ERR_INVALID_ARG, "oat_plan_query: NULL plan or stats");
+    st->n_radius_classes = p->n_cls;
+    st->n_rings = p->n_rings;
+    st->points_ball = p->points_ball;
+    st->points_grid = -1;
+    st->table_bytes = p->table_bytes;
+    st->scratch_bytes = p->scratch_bytes;
+    st->work_items = p->n_items;
+    if (want_count) {
+        DeviceGuard dg(p->device);
+        if (dg.err != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_plan_query: ") + cudaGetErrorString(dg.err));
+        long long n = 0;
+        int rc = oat::count_grid_points(*p, &n);
+        if (rc != OAT_OK) return rc;
+        st->points_grid = n;
+    }
+    return OAT_OK;
+}
+
+int oat_plan_set_profiling(oat_plan plan, int enable) {
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p) return set_error(OAT_ERR_INVALID_ARG, "oat_plan_set_profiling: NULL plan");
+    if (enable && p->ev[0].empty()) {
+        DeviceGuard dg(p->device);
+        for (int w = 0; w < 2; ++w) {
+            p->ev[w].resize(2 * kMaxEvents);
+            for (auto &e : p->ev[w]) {
+                cudaError_t err = cudaEventCreate(&e);
+                if (err != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_plan_set_profiling: ") + cudaGetErrorString(err));
+            }
+        }
+    }
+    p->profiling = enable != 0;
+    return OAT_OK;
+}
+
+int oat_plan_kernel_time(oat_plan plan, int which, int reset, double *ms, long long *launches) {
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || which < 0 || which > 1) return set_error(OAT_ERR_INVALID_ARG, "oat_plan_kernel_time: bad plan or kernel index");
+    DeviceGuard dg(p->device);
+    for (int i = 0; i + 1 < p->ev_used[which]; i += 2) {
+        cudaError_t e = cudaEventSynchronize(p->ev[which][i + 1]);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, p->ev[which][i], p->ev[which][i + 1]);
+        if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_plan_kernel_time: ") + cudaGetErrorString(e));
+        p->ms_acc[which] += t;
+        p->launches[which] += 1;
+    }
+    p->ev_used[which] = 0;
+    if (ms) *ms = p->ms_acc[which];
+    if (launches) *launches = p->launches[which];
+    if (reset) { p->ms_acc[which] = 0; p->launches[which] = 0; }
+    return OAT_OK;
+}
+
+}  // extern "C"

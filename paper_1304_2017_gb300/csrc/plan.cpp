@@ -1,0 +1,273 @@
+// Host side of a plan: validation, the FP64 shell-lattice tables (Appendix), work items and
+// device upload.  Compiled without floating-point contraction so that the integer lattice
+// counts N_i and N_j come out of plain IEEE double arithmetic in the paper's formula order.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+
+#include "oat_internal.h"
+
+namespace oat {
+
+namespace {
+
+constexpr int kTileQ = 8;   // transducers of one radius class per forward work item
+
+bool finite3(const double *v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+// Radius of the origin-centred sphere containing the node cuboid grown by one spacing.
+double default_support_radius(const oat_geometry &g) {
+    double best = 0.0;
+    const double lo[3] = {g.origin_mm[0] - g.spacing_mm, g.origin_mm[1] - g.spacing_mm, g.origin_mm[2] - g.spacing_mm};
+    const double hi[3] = {g.origin_mm[0] + g.spacing_mm * g.nx, g.origin_mm[1] + g.spacing_mm * g.ny,
+                          g.origin_mm[2] + g.spacing_mm * g.nz};
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int c = 0; c < 2; ++c) {
+                double x = a ? hi[0] : lo[0], y = b ? hi[1] : lo[1], z = c ? hi[2] : lo[2];
+                best = std::max(best, std::sqrt(x * x + y * y + z * z));
+            }
+    return best;
+}
+
+// Local frame of a transducer at r (Appendix): e_z towards the origin, e_y = unit(z x r),
+// or (0,1,0) on the z axis, e_x = e_y x e_z.
+void frame(const double *r, double ex[3], double ey[3], double ez[3], double *rs) {
+    double n = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    *rs = n;
+    ez[0] = -r[0] / n; ez[1] = -r[1] / n; ez[2] = -r[2] / n;
+    double a = -r[1] / n, b = r[0] / n;
+    double m = std::sqrt(a * a + b * b);
+    if (m > 0.0) { ey[0] = a / m; ey[1] = b / m; ey[2] = 0.0; }
+    else { ey[0] = 0.0; ey[1] = 1.0; ey[2] = 0.0; }
+    ex[0] = ey[1] * ez[2] - ey[2] * ez[1];
+    ex[1] = ey[2] * ez[0] - ey[0] * ez[2];
+    ex[2] = ey[0] * ez[1] - ey[1] * ez[0];
+}
+
+template <class T>
+size_t push_bytes(std::vector<unsigned char> &blob, const std::vector<T> &v) {
+    size_t off = (blob.size() + 255) & ~size_t(255);
+    blob.resize(off + v.size() * sizeof(T));
+    if (!v.empty()) std::memcpy(blob.data() + off, v.data(), v.size() * sizeof(T));
+    return off;
+}
+
+}  // namespace
+
+int plan_create(const oat_geometry *gin, int device, Plan **out) {
+    *out = nullptr;
+    if (!gin) return set_error(OAT_ERR_INVALID_ARG, "oat_plan_create: geometry is NULL");
+    const oat_geometry &g = *gin;
+    if (g.nx < 1 || g.ny < 1 || g.nz < 1)
+        return set_error(OAT_ERR_INVALID_ARG, "oat_plan_create: nx, ny, nz must be >= 1");
+    if ((long long)g.nx * g.ny * g.nz >= (1LL << 31) ||
+        (long long)(g.nx + 1) * (g.ny + 1) * (g.nz + 1) * 8 >= (1LL << 31))
+        return set_error(OAT_ERR_INVALID_ARG, "oat_plan_create: grid too large (nx*ny*nz must stay below 2^28)");
+    if (g.n_transducers < 1 || !g.positions_mm)
+        return set_error(OAT_ERR_INVALID_ARG, "oat_plan_create: need n_transducers >= 1 and positions_mm");
+    if (g.n_samples < 1 || (g.apply_d && g.n_samples < 3))
+        return set_error(OAT_ERR_INVALID_ARG, "oat_plan_create: n_samples must be >= 1 (>= 3 with apply_d)");
+    if ((long long)g.n_transducers * g.n_samples >= (1LL << 31))
+        return set_error(OAT_ERR_INVALID_ARG, "oat_plan_create: n_transducers * n_samples must be < 2^31");
+    if (!(std::isfinite(g.spacing_mm) && g.spacing_mm > 0) || !(std::isfinite(g.fs_mhz) && g.fs_mhz > 0) ||
+        !(std::isfinite(g.c_mm_per_us) && g.c_mm_per_us > 0) || !(std::isfinite(g.t_min_us) && g.t_min_us >= 0) ||
+        !std::isfinite(g.support_radius_mm) || !std::isfinite(g.gruneisen) || !finite3(g.origin_mm))
+        return set_error(OAT_ERR_INVALID_ARG, "oat_plan_create: spacing, fs, c must be finite and > 0, t_min >= 0, "
+                                              "support radius, gruneisen and origin finite");
+    if (g.data_dtype != OAT_F32 && g.data_dtype != OAT_F16 && g.data_dtype != OAT_BF16)
+        return set_error(OAT_ERR_INVALID_ARG, "oat_plan_create: data_dtype must be OAT_F32, OAT_F16 or OAT_BF16");
+    if (g.apply_d != 0 && g.apply_d != 1)
+        return set_error(OAT_ERR_INVALID_ARG, "oat_plan_create: apply_d must be 0 or 1");
+
+    Plan *p = new (std::nothrow) Plan();
+    if (!p) return set_error(OAT_ERR_OOM, "oat_plan_create: host allocation failed");
+    p->g = g;
+    p->Q = g.n_transducers; p->K = g.n_samples;
+    p->nx = g.nx; p->ny = g.ny; p->nz = g.nz;
+    p->pos.assign(g.positions_mm, g.positions_mm + 3 * (size_t)p->Q);
+    p->g.positions_mm = p->pos.data();
+    p->device = device;
+    for (int q = 0; q < p->Q; ++q)
+        if (!finite3(&p->pos[3 * q])) { delete p; return set_error(OAT_ERR_INVALID_ARG, "oat_plan_create: non-finite transducer position"); }
+
+    p->R = g.support_radius_mm > 0 ? g.support_radius_mm : default_support_radius(g);
+    p->dt = 1.0 / g.fs_mhz;
+    p->cd = g.gruneisen / (8.0 * M_PI * g.c_mm_per_us * g.c_mm_per_us * p->dt * p->dt);
+    const double ds = g.spacing_mm;
+    for (int d = 0; d < 3; ++d) p->O[d] = (float)(-g.origin_mm[d] / ds);
+    p->ds2 = (float)(ds * ds);
+    p->R0 = (float)(g.c_mm_per_us * g.t_min_us / ds);
+    p->dR = (float)(g.c_mm_per_us * p->dt / ds);
+
+    // transducers: frames and radius classes (exact equality of |r_q| in double)
+    const int Q = p->Q, K = p->K;
+    std::vector<Xdcr> xd(Q);
+    std::vector<double> rs(Q);
+    std::map<double, int> cls_of;
+    for (int q = 0; q < Q; ++q) {
+        double ex[3], ey[3], ez[3];
+        frame(&p->pos[3 * q], ex, ey, ez, &rs[q]);
+        if (!(rs[q] > p->R)) {
+            delete p;
+            return set_error(OAT_ERR_GEOMETRY, "oat_plan_create: transducer " + std::to_string(q) +
+                                                   " is not outside the support sphere (|r_q| <= R)");
+        }
+        for (int d = 0; d < 3; ++d) { xd[q].ex[d] = (float)ex[d]; xd[q].ey[d] = (float)ey[d]; xd[q].ez[d] = (float)ez[d]; }
+        xd[q].dist = (float)(rs[q] / ds);
+        cls_of.emplace(rs[q], 0);
+    }
+    std::vector<double> cls_r;
+    for (auto &kv : cls_of) { kv.second = (int)cls_r.size(); cls_r.push_back(kv.first); }
+    p->n_cls = (int)cls_r.size();
+    for (int q = 0; q < Q; ++q) xd[q].cls = cls_of[rs[q]];
+
+    // shell lattice per (class, k): rings i < N_i with N_j points each
+    const int C = p->n_cls;
+    std::vector<Ring> rings;
+    std::vector<int> ring_off((size_t)C * K), ring_cnt((size_t)C * K);
+    p->cls_points.assign((size_t)C * K, 0);
+    for (int c = 0; c < C; ++c) {
+        const double r_s = cls_r[c];
+        for (int k = 0; k < K; ++k) {
+            const size_t ck = (size_t)c * K + k;
+            ring_off[ck] = (int)rings.size();
+            ring_cnt[ck] = 0;
+            double t = g.t_min_us + k * p->dt;
+            double rho = g.c_mm_per_us * t;
+            if (!(rho > 0.0)) continue;
+            double arg = (r_s * r_s + rho * rho - p->R * p->R) / (2.0 * rho * r_s);
+            if (arg > 1.0) continue;
+            double thmax = (arg < -1.0) ? M_PI : std::acos(arg);
+            double dth = ds / rho;
+            int ni = (int)std::floor(thmax / dth);
+            if (rings.size() + (size_t)ni >= (size_t)INT32_MAX) {
+                delete p;
+                return set_error(OAT_ERR_UNSUPPORTED, "oat_plan_create: lattice tables exceed 2^31 rings");
+            }
+            long long npts = 0;
+            for (int i = 0; i < ni; ++i) {
+                double th = i * dth;
+                double st = std::sin(th);
+                double dph = ds / (rho * st);
+                int nj = (int)std::floor(2.0 * M_PI / dph);
+                Ring rr;
+                rr.h = (float)((rho * std::cos(th) - r_s) / ds);
+                rr.a = (float)(rho * st / ds);
+                rr.dphi = (float)dph;
+                rr.nj = nj;
+                if (nj == 0) { rr.dphi = 0.f; rr.a = 0.f; }
+                rings.push_back(rr);
+                npts += nj;
+            }
+            ring_cnt[ck] = ni;
+            p->cls_points[ck] = npts;
+        }
+    }
+    p->n_rings = (long long)rings.size();
+
+    // transducers sorted by class; forward work items (class, k, tile) heaviest shells first
+    std::vector<int> qlist(Q);
+    for (int q = 0; q < Q; ++q) qlist[q] = q;
+    std::stable_sort(qlist.begin(), qlist.end(), [&](int a, int b) { return xd[a].cls < xd[b].cls; });
+    std::vector<int> cls_start(C + 1, 0), cls_n(C, 0);
+    for (int q = 0; q < Q; ++q) cls_n[xd[q].cls]++;
+    for (int c = 0; c < C; ++c) cls_start[c + 1] = cls_start[c] + cls_n[c];
+    std::vector<int4> items;
+    p->points_ball = 0;
+    for (int c = 0; c < C; ++c)
+        for (int k = 0; k < K; ++k) {
+            long long np = p->cls_points[(size_t)c * K + k];
+            p->points_ball += np * cls_n[c];
+            if (np == 0) continue;
+            for (int s = 0; s < cls_n[c]; s += kTileQ)
+                items.push_back(make_int4(c, k, cls_start[c] + s, std::min(kTileQ, cls_n[c] - s)));
+        }
+    if (p->points_ball == 0) {
+        delete p;
+        return set_error(OAT_ERR_GEOMETRY, "oat_plan_create: no shell of the time window meets the support sphere");
+    }
+    std::stable_sort(items.begin(), items.end(), [&](const int4 &a, const int4 &b) {
+        return p->cls_points[(size_t)a.x * K + a.y] > p->cls_points[(size_t)b.x * K + b.y];
+    });
+    p->n_items = (long long)items.size();
+    if (p->n_items >= (1LL << 31)) {
+        delete p;
+        return set_error(OAT_ERR_UNSUPPORTED, "oat_plan_create: too many work items");
+    }
+
+    std::vector<float> Rk(K), wD(K);
+    std::vector<double> wD64(K);
+    for (int k = 0; k < K; ++k) {
+        double t = g.t_min_us + k * p->dt;
+        Rk[k] = (float)(g.c_mm_per_us * t / ds);
+        double tau = g.t_min_us / p->dt + k;
+        wD[k] = tau > 0.0 ? (float)(p->cd / tau) : 0.f;
+        wD64[k] = tau > 0.0 ? p->cd / tau : 0.0;
+    }
+
+    // one device blob for every table
+    std::vector<unsigned char> blob;
+    size_t o_rings = push_bytes(blob, rings), o_off = push_bytes(blob, ring_off), o_cnt = push_bytes(blob, ring_cnt);
+    size_t o_xd = push_bytes(blob, xd), o_ql = push_bytes(blob, qlist), o_it = push_bytes(blob, items);
+    size_t o_rk = push_bytes(blob, Rk), o_wd = push_bytes(blob, wD), o_wd64 = push_bytes(blob, wD64);
+    p->table_bytes = (long long)blob.size();
+
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) {
+        delete p;
+        return set_error(OAT_ERR_CUDA, std::string("oat_plan_create: cudaSetDevice: ") + cudaGetErrorString(e));
+    }
+    auto fail = [&](cudaError_t err, const char *what) {
+        int code = (err == cudaErrorMemoryAllocation) ? OAT_ERR_OOM : OAT_ERR_CUDA;
+        if (p->d_tables) cudaFree(p->d_tables);
+        if (p->d_g) cudaFree(p->d_g);
+        if (p->d_part) cudaFree(p->d_part);
+        delete p;
+        cudaGetLastError();
+        cudaSetDevice(prev);
+        return set_error(code, std::string("oat_plan_create: ") + what + ": " + cudaGetErrorString(err));
+    };
+    if ((e = cudaMalloc(&p->d_tables, blob.size())) != cudaSuccess) return fail(e, "cudaMalloc(tables)");
+    if ((e = cudaMemcpy(p->d_tables, blob.data(), blob.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(e, "cudaMemcpy(tables)");
+    size_t g_bytes = sizeof(double) * (size_t)Q * K;
+    size_t part_bytes = sizeof(float) * 8 * (size_t)(p->nx + 1) * (p->ny + 1) * (p->nz + 1);
+    if ((e = cudaMalloc(&p->d_g, g_bytes)) != cudaSuccess) return fail(e, "cudaMalloc(g scratch)");
+    if ((e = cudaMalloc(&p->d_part, part_bytes)) != cudaSuccess) return fail(e, "cudaMalloc(G^T scratch)");
+    p->scratch_bytes = (long long)(g_bytes + part_bytes);
+    cudaSetDevice(prev);
+
+    unsigned char *base = (unsigned char *)p->d_tables;
+    p->t.rings = (const Ring *)(base + o_rings);
+    p->t.ring_off = (const int *)(base + o_off);
+    p->t.ring_cnt = (const int *)(base + o_cnt);
+    p->t.xd = (const Xdcr *)(base + o_xd);
+    p->t.qlist = (const int *)(base + o_ql);
+    p->t.items = (const int4 *)(base + o_it);
+    p->t.Rk = (const float *)(base + o_rk);
+    p->t.wD = (const float *)(base + o_wd);
+    p->t.wD64 = (const double *)(base + o_wd64);
+    *out = p;
+    return OAT_OK;
+}
+
+void plan_destroy(Plan *p) {
+    if (!p) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(p->device);
+    for (int w = 0; w < 2; ++w)
+        for (cudaEvent_t e : p->ev[w]) cudaEventDestroy(e);
+    if (p->d_tables) cudaFree(p->d_tables);
+    if (p->d_g) cudaFree(p->d_g);
+    if (p->d_part) cudaFree(p->d_part);
+    cudaSetDevice(prev);
+    delete p;
+}
+
+}  // namespace oat

@@ -1,0 +1,203 @@
+"""Python binding of the C ABI in include/oat.h (argument marshalling only).
+
+The functions carry the C names (``oat_plan_create``, ``oat_project``, ``oat_backproject``,
+``oat_plan_destroy``, ``oat_plan_query``, ...).  ``Plan`` wraps a plan handle for torch
+tensors: device memory and the current CUDA stream come from PyTorch, every step of the
+operator runs in the library's sm_103a kernels.  There is no CPU fallback: importing this
+module fails loudly when ``liboat.so`` has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liboat.so")
+
+OAT_OK = 0
+OAT_ERR_INVALID_ARG = -1
+OAT_ERR_GEOMETRY = -2
+OAT_ERR_CUDA = -3
+OAT_ERR_OOM = -4
+OAT_ERR_UNSUPPORTED = -5
+OAT_F32, OAT_F16, OAT_BF16 = 0, 1, 2
+
+
+class OatError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class oat_geometry(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("spacing_mm", ctypes.c_double), ("origin_mm", ctypes.c_double * 3),
+                ("n_transducers", ctypes.c_int), ("positions_mm", ctypes.POINTER(ctypes.c_double)),
+                ("n_samples", ctypes.c_int), ("fs_mhz", ctypes.c_double), ("t_min_us", ctypes.c_double),
+                ("c_mm_per_us", ctypes.c_double), ("support_radius_mm", ctypes.c_double),
+                ("gruneisen", ctypes.c_double), ("data_dtype", ctypes.c_int), ("apply_d", ctypes.c_int)]
+
+
+class oat_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_longlong) for n in ("n_radius_classes", "n_rings", "points_ball", "points_grid",
+                                                  "table_bytes", "scratch_bytes", "work_items")]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'` "
+                          "(the projector has no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp = ctypes.c_void_p
+    lib.oat_plan_create.argtypes = [ctypes.POINTER(oat_geometry), ctypes.c_int, ctypes.POINTER(vp)]
+    lib.oat_plan_destroy.argtypes = [vp]
+    lib.oat_project.argtypes = [vp, vp, vp, vp]
+    lib.oat_backproject.argtypes = [vp, vp, vp, vp]
+    lib.oat_plan_query.argtypes = [vp, ctypes.c_int, ctypes.POINTER(oat_stats)]
+    lib.oat_plan_set_profiling.argtypes = [vp, ctypes.c_int]
+    lib.oat_plan_kernel_time.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_longlong)]
+    lib.oat_last_error.restype = ctypes.c_char_p
+    lib.oat_version.restype = ctypes.c_int
+    for name in ("oat_plan_create", "oat_plan_destroy", "oat_project", "oat_backproject", "oat_plan_query",
+                 "oat_plan_set_profiling", "oat_plan_kernel_time"):
+        getattr(lib, name).restype = ctypes.c_int
+    return lib
+
+
+lib = _load()
+
+
+def _check(rc):
+    if rc != OAT_OK:
+        raise OatError(rc, lib.oat_last_error().decode())
+    return rc
+
+
+def make_geometry_struct(geom, data_dtype=OAT_F32, apply_d=True):
+    """oat_geometry from a workloads.Geometry; returns (struct, positions array kept alive)."""
+    pos = np.ascontiguousarray(geom.positions_mm, dtype=np.float64)
+    s = oat_geometry(geom.nx, geom.ny, geom.nz, geom.spacing_mm, (ctypes.c_double * 3)(*geom.origin_mm),
+                     pos.shape[0], pos.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), geom.n_samples,
+                     geom.fs_mhz, geom.t_min_us, geom.c_mm_per_us, geom.support_radius_mm, geom.gruneisen,
+                     int(data_dtype), int(bool(apply_d)))
+    return s, pos
+
+
+# ---- C names ---------------------------------------------------------------------------
+
+def oat_version():
+    return lib.oat_version()
+
+
+def oat_last_error():
+    return lib.oat_last_error().decode()
+
+
+def oat_plan_create(geom_struct, device=0):
+    h = ctypes.c_void_p()
+    _check(lib.oat_plan_create(ctypes.byref(geom_struct), int(device), ctypes.byref(h)))
+    return h
+
+
+def oat_plan_destroy(handle):
+    return _check(lib.oat_plan_destroy(handle))
+
+
+def oat_project(handle, d_vol, d_data, stream=0):
+    return _check(lib.oat_project(handle, ctypes.c_void_p(d_vol), ctypes.c_void_p(d_data), ctypes.c_void_p(stream)))
+
+
+def oat_backproject(handle, d_data, d_vol, stream=0):
+    return _check(lib.oat_backproject(handle, ctypes.c_void_p(d_data), ctypes.c_void_p(d_vol), ctypes.c_void_p(stream)))
+
+
+def oat_plan_query(handle, count_grid_points=False):
+    st = oat_stats()
+    _check(lib.oat_plan_query(handle, int(bool(count_grid_points)), ctypes.byref(st)))
+    return {n: getattr(st, n) for n, _ in oat_stats._fields_}
+
+
+def oat_plan_set_profiling(handle, enable=True):
+    return _check(lib.oat_plan_set_profiling(handle, int(bool(enable))))
+
+
+def oat_plan_kernel_time(handle, which, reset=False):
+    ms, n = ctypes.c_double(), ctypes.c_longlong()
+    _check(lib.oat_plan_kernel_time(handle, int(which), int(bool(reset)), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+# ---- torch wrapper ---------------------------------------------------------------------
+
+_DT = {OAT_F32: "float32", OAT_F16: "float16", OAT_BF16: "bfloat16"}
+
+
+class Plan:
+    """A plan for one geometry: ``project(vol) -> data`` and ``backproject(data) -> vol``."""
+
+    def __init__(self, geom, data_dtype=OAT_F32, apply_d=True, device=None):
+        import torch
+        self._torch = torch
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(device)
+        self.geom = geom
+        self.data_dtype = int(data_dtype)
+        self.apply_d = bool(apply_d)
+        self._s, self._pos = make_geometry_struct(geom, data_dtype, apply_d)
+        self.handle = oat_plan_create(self._s, self.device)
+        self.vol_shape = (geom.nz, geom.ny, geom.nx)
+        self.data_shape = (geom.n_transducers, geom.n_samples)
+        self.torch_data_dtype = getattr(torch, _DT[self.data_dtype])
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            oat_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self):
+        return self._torch.cuda.current_stream(self.device).cuda_stream
+
+    def _checked(self, t, shape, dtype, name):
+        torch = self._torch
+        if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.device.index != self.device:
+            raise ValueError(f"{name}: expected a CUDA tensor on device {self.device}")
+        if tuple(t.shape) != tuple(shape) or t.dtype != dtype or not t.is_contiguous():
+            raise ValueError(f"{name}: expected contiguous {dtype} {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
+        return t
+
+    def project(self, vol, out=None):
+        torch = self._torch
+        self._checked(vol, self.vol_shape, torch.float32, "vol")
+        if out is None:
+            out = torch.empty(self.data_shape, dtype=self.torch_data_dtype, device=vol.device)
+        self._checked(out, self.data_shape, self.torch_data_dtype, "out")
+        oat_project(self.handle, vol.data_ptr(), out.data_ptr(), self._stream())
+        return out
+
+    def backproject(self, data, out=None):
+        torch = self._torch
+        self._checked(data, self.data_shape, self.torch_data_dtype, "data")
+        if out is None:
+            out = torch.empty(self.vol_shape, dtype=torch.float32, device=data.device)
+        self._checked(out, self.vol_shape, torch.float32, "out")
+        oat_backproject(self.handle, data.data_ptr(), out.data_ptr(), self._stream())
+        return out
+
+    def stats(self, count_grid_points=False):
+        return oat_plan_query(self.handle, count_grid_points)
+
+    def set_profiling(self, enable=True):
+        oat_plan_set_profiling(self.handle, enable)
+
+    def kernel_time(self, which, reset=False):
+        return oat_plan_kernel_time(self.handle, which, reset)
