@@ -1,0 +1,308 @@
+"""Benchmark of the H / H^T pair on the 256^3 spherical-aperture scan.
+
+A step is one projection u = H alpha and one backprojection alpha' = H^T y over the 256^3 @ 0.2 mm
+grid, 128 rings x 180 views (23,040 point transducers on a 65 mm sphere), 1536 samples at 20 MHz.
+The metric counts G interpolations: the lattice points whose trilinear stencil touches the grid,
+once for H and once for H^T per step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  With torchrun (N > 1) every rank runs an independent replica of the
+problem (the operator needs no exchange); the value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H+H^T G interp-samples/s and % HBM/L2 roofline; PLS-TV time to 1e-3 residual"
+UNIT = "interp-samples/s"
+WORKLOAD = "256^3 @ 0.2 mm, 200 ellipsoids, 128 rings x 180 views (23040 transducers) on 65 mm, K=1536 @ 20 MHz, c=1.5"
+# FP32 operations charged to one interpolated sample ("Roofline"): lattice point
+# 6 FMA (12), floor 3, fraction 3, 7 lerps (7 sub + 7 FMA = 21), accumulate 1.
+FLOP_PER_SAMPLE = 40.0
+N_SM = 152
+# kernels of this library per step: k_radial_gather, k_apply_d_dbl (H); k_absmax, k_brick_gather_t,
+# k_finish_t (H^T)
+LAUNCHES_PER_STEP = 5
+FP32_LANES_PER_SM = 128
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            mp = json.load(f)
+        return mp, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(geom, alpha, y, n_xdcr=32, points_per_xdcr=None):
+    """Time the FP64 oracle (as it stands) for H and H^T on a transducer subset of the workload."""
+    import oracle
+    qs = np.linspace(0, geom.n_transducers - 1, n_xdcr).round().astype(int)
+    sub = geom.subset(qs)
+    ys = np.ascontiguousarray(y[qs], dtype=np.float64)
+    a64 = alpha.astype(np.float64)
+    threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    oracle.H(sub, a64)
+    oracle.Ht(sub, ys)
+    dt = time.perf_counter() - t0
+    pts = points_per_xdcr * n_xdcr if points_per_xdcr is not None else oracle.count_points(sub)[1]
+    return {"value": 2.0 * pts / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n_xdcr} of {geom.n_transducers} transducers (evenly spaced), full grid and time window; "
+                      f"one H + one H^T in FP64, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle on the host cores, on the same workload, metric and unit (bounded sample per step)."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    from paper_1304_2017_gb300 import workloads as W
+    import oracle
+    geom = W.config("c2")
+    alpha = W.phantom("c2", geom)
+    y = W.random_data(geom, seed=7)
+    n_x = int(os.environ.get("OAT_REF_XDCR", "8"))
+    qs = np.linspace(0, geom.n_transducers - 1, n_x).round().astype(int)
+    sub = geom.subset(qs)
+    pts = oracle.count_points(sub)[1]
+    a64 = alpha.astype(np.float64)
+    ys = np.ascontiguousarray(y[qs], dtype=np.float64)
+    for _ in range(args.warmup):
+        oracle.H(sub, a64)
+        oracle.Ht(sub, ys)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.H(sub, a64)
+        oracle.Ht(sub, ys)
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    value = 2.0 * pts / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{n_x} evenly spaced transducers per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": f"{n_x} of {geom.n_transducers} transducers, full grid and window"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1304_2017_gb300 import oat
+    from paper_1304_2017_gb300 import workloads as W
+
+    world, rank, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    geom = W.config(args.config)
+    alpha_np = W.phantom(args.config, geom, seed=1304 + rank)
+    y_np = W.random_data(geom, seed=7 + rank)
+    plan = oat.Plan(geom, device=local)
+    st = plan.stats(count_grid_points=True)
+    pts = st["points_grid"]
+    alpha = torch.from_numpy(alpha_np).to(dev)
+    y = torch.from_numpy(y_np).to(dev)
+    u = torch.empty(plan.data_shape, dtype=torch.float32, device=dev)
+    a = torch.empty(plan.vol_shape, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.project(alpha, out=u)
+        plan.backproject(y, out=a)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step()
+    plan.set_profiling(True)
+    plan.kernel_time(0, reset=True)
+    plan.kernel_time(1, reset=True)
+    barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    plan.set_profiling(False)
+    g_ms, g_n = plan.kernel_time(0, reset=True)
+    b_ms, b_n = plan.kernel_time(1, reset=True)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * 2.0 * pts / (ms_max * 1e-3)
+
+    # end to end through the public API with host buffers: pinned H2D of alpha and y, H and
+    # H^T, D2H of u and alpha'
+    h_alpha = torch.from_numpy(alpha_np).pin_memory()
+    h_y = torch.from_numpy(y_np).pin_memory()
+    h_u = torch.empty(plan.data_shape, dtype=torch.float32).pin_memory()
+    h_a = torch.empty(plan.vol_shape, dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        alpha.copy_(h_alpha, non_blocking=True)
+        y.copy_(h_y, non_blocking=True)
+        step()
+        h_u.copy_(u, non_blocking=True)
+        h_a.copy_(a, non_blocking=True)
+
+    e2e_step()
+    barrier()
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
+    t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = world * 2.0 * pts / (float(t.item()) * 1e-3)
+    bi = h_alpha.numel() * 4 + h_y.numel() * 4
+    bo = h_u.numel() * 4 + h_a.numel() * 4
+
+    # roofline of the dominant kernel, timed by events around its launches on the call's stream
+    dom_ms, dom_name = (b_ms / max(b_n, 1), "k_brick_gather_t (H^T)") if b_ms >= g_ms else (g_ms / max(g_n, 1), "k_radial_gather (H)")
+    peaks, src = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = FLOP_PER_SAMPLE * pts / (dom_ms * 1e-3) / 1e12
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            with open(tpath) as f:
+                traffic = json.load(f).get(dom_name.split()[0])
+        except (OSError, ValueError):
+            traffic = None
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops, "traffic": traffic, "kernel": dom_name,
+            "kernel_ms": dom_ms, "peak_source": f"{src}: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
+            "flop_per_sample": FLOP_PER_SAMPLE}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [geom.nx, geom.ny, geom.nz], "transducers": geom.n_transducers,
+                       "samples": geom.n_samples, "points_per_operator": pts,
+                       "l2": "inputs larger than L2 (volume 67 MB + data 142 MB per step)",
+                       "parallelism": f"replicas x{world}"},
+            "gpu_launches": args.steps * LAUNCHES_PER_STEP,
+            "kernel_ms": {"k_radial_gather": g_ms / max(g_n, 1), "k_brick_gather_t": b_ms / max(b_n, 1)},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
+            "roofline": roof, "clocks": clocks}
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline(geom, alpha_np, y_np, n_xdcr=int(os.environ.get("OAT_CPU_XDCR", "16")))
+        except Exception as exc:  # the baseline must not hide the GPU line
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {exc}"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

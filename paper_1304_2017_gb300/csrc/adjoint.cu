@@ -1,36 +1,45 @@
-// Backprojector alpha' = G^T D^T y as a gather per voxel, no floating-point atomics.
+// Backprojector alpha' = G^T D^T y (adjoints of Eqs. dis_srt and dis_g2p), no floating-point
+// atomics.
 //
 // A lattice point P of (q, k) contributes Delta_s^2 g'_{q,k} psi_n(P) to the eight nodes n of
-// the cell m = floor(P) that contains it (Eq. expfunI; adjoint of Eq. dis_srt).  Points are
-// partitioned by their cell, so:
+// the cell floor(P) (Eq. expfunI), with g'_{q,k} = (C_D / tau_k)(m_{k-1} y_{k-1} -
+// m_{k+1} y_{k+1}), m_j = [1 <= j <= K-2] (the exact transpose of the projector's D), read
+// straight from y.
 //
-// k_cell_gather: one thread per cell m in [-1, n-1]^3.  For every transducer q the thread
-//   enumerates the lattice points that can lie in its cell -- shells k whose radius is within
-//   the cell's circumscribed radius of the cell centre, rings i of those shells whose polar
-//   angle is within the angle the cell subtends, and on each ring the azimuth window whose
-//   points are within that radius (exact point-to-ring-distance condition) -- evaluates each
-//   candidate with the SAME FP32 lattice-point function as the projector, keeps those with
-//   floor(P) == m, and accumulates the eight trilinear weights times g'_{q,k} into eight
-//   per-corner partial sums held in registers.  g'_{q,k} = (C_D / tau_k)(m_{k-1} y_{k-1} -
-//   m_{k+1} y_{k+1}) is read straight from y (D^T fused into the input read).
-//   Output: per-cell corner partials, scratch [cells][8].
-//
-// k_combine: each node sums the partials of its eight adjacent cells (written once).
+// k_brick_gather_t  one thread block per brick of kBA^3 cells (and range of transducers).  The
+//                   block walks, transducer by transducer, the lattice points that can lie in
+//                   the brick (brick.cuh), evaluates each with the lattice-point functions shared
+//                   with the projector, and for the points whose cell lies in the brick adds the
+//                   eight weights w_c g'_{q,k}, rounded to a fixed-point unit chosen from max|y|,
+//                   to the brick's (kBA+1)^3 node sums with 32-bit integer shared-memory atomics.
+//                   Integer addition is exact and associative, so the sums do not depend on the
+//                   order of the points.  After each bounded pass of transducers the node sums
+//                   are folded into the volume's 64-bit accumulator (integer global atomics: the
+//                   nodes on brick faces are shared with neighbouring bricks).
+// k_finish_t        alpha'_n = sum_n / scale * Delta_s^2 as float32: every voxel written once.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
-#include "oat_internal.h"
+#include "brick.cuh"
 
 namespace oat {
+
+constexpr int kAdjThreads = 512;
+constexpr int kAdjLanesPerRing = 16;
+
+__global__ void k_absmax(const void *__restrict__ x, size_t n, int dtype, unsigned int *out);
 
 struct AdjArgs {
     DevTables t;
     const void *y;
-    float *part;
+    unsigned long long *vacc;     // [N] fixed-point node sums
+    const unsigned int *amax;     // bits of max |y|
     int nx, ny, nz, K, Q;
+    int nb[3], bs[3];
+    int qchunk, kspan, qpass;
     float O[3];
     float R0, dR;
-    float ds2;
+    float gscale;                 // max |g'| / max |y|
     int apply_d;
 };
 
@@ -53,154 +62,155 @@ __device__ __forceinline__ float gprime(const AdjArgs &a, int q, int k) {
     return w * (lo - hi);
 }
 
-constexpr float kCellR = 0.8700f;        // > sqrt(3)/2: circumscribed radius of a unit cell + margin
-constexpr float kTwoPi = 6.28318530717958647692f;
+// Node sums of one pass live in shared memory as two 32-bit integer halves of the
+// fixed-point value v (|v| <= 2^30): hi = v >> 15 (arithmetic) and lo = v & 0x7fff, each added
+// with a native 32-bit integer atomic.  A pass is bounded so that neither half can overflow
+// (at most 2^15 contributions per node); the halves are then folded into the 64-bit volume
+// accumulator and cleared.
+__device__ __forceinline__ void sadd(int *hi, unsigned int *lo, int idx, float x) {
+    const int v = __float2int_rn(x);
+    if (v != 0) {
+        atomicAdd(hi + idx, v >> 15);
+        atomicAdd(lo + idx, (unsigned int)(v & 0x7fff));
+    }
+}
 
-template <int DT>
-__global__ void __launch_bounds__(128) k_cell_gather(AdjArgs a) {
-    const int cx = a.nx + 1, cy = a.ny + 1, cz = a.nz + 1;
-    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= cx * cy * cz) return;
-    const int mx = cell % cx - 1, my = (cell / cx) % cy - 1, mz = cell / (cx * cy) - 1;
-    // cell centre relative to the global origin, index units
-    const float Xg0 = (float)mx + 0.5f - a.O[0], Xg1 = (float)my + 0.5f - a.O[1], Xg2 = (float)mz + 0.5f - a.O[2];
-    const float rc2 = kCellR * kCellR;
+template <int B, int DT>
+__global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
+    extern __shared__ int shi[];   // (B+1)^3 high halves, then (B+1)^3 low halves
+    constexpr int S1 = B + 1, S2 = (B + 1) * (B + 1), NN = (B + 1) * (B + 1) * (B + 1);
+    unsigned int *slo = (unsigned int *)(shi + NN);
+    const int nqc = (a.Q + a.qchunk - 1) / a.qchunk;
+    const int brick = blockIdx.x / nqc;
+    const int q0 = (blockIdx.x % nqc) * a.qchunk;
+    const int q1 = min(a.Q, q0 + a.qchunk);
+    int L[3], E[3];
+    {
+        const int n[3] = {a.nx, a.ny, a.nz};
+        brick_box(brick, a.nb, a.bs, n, L, E);
+    }
+    for (int idx = threadIdx.x; idx < NN; idx += blockDim.x) { shi[idx] = 0; slo[idx] = 0u; }
+    __syncthreads();
 
-    float acc[8], outer[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) { acc[c] = 0.f; outer[c] = 0.f; }
+    // bounding sphere of the brick's cells [L, L + E)
+    const float c[3] = {L[0] + 0.5f * E[0], L[1] + 0.5f * E[1], L[2] + 0.5f * E[2]};
+    const float rb = 0.5f * sqrtf((float)(E[0] * E[0] + E[1] * E[1] + E[2] * E[2])) + 0.05f;
+    const float rb2 = rb * rb;
+    // contributions |w g'| <= max|g'| map to at most 2^30 units
+    const float scale = (float)pow2_scale((double)__uint_as_float(*a.amax) * (double)a.gscale, 30);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int sub = lane / kAdjLanesPerRing, sl = lane % kAdjLanesPerRing;
+    constexpr int kSubs = 32 / kAdjLanesPerRing;
 
-    for (int q = 0; q < a.Q; ++q) {
-        const Xdcr &x = a.t.xd[q];
-        // cell centre in the transducer's local frame (transducer at the local origin)
-        const float vx = Xg0 * x.ex[0] + Xg1 * x.ex[1] + Xg2 * x.ex[2];
-        const float vy = Xg0 * x.ey[0] + Xg1 * x.ey[1] + Xg2 * x.ey[2];
-        const float vz0 = Xg0 * x.ez[0] + Xg1 * x.ez[1] + Xg2 * x.ez[2];
-        const float vz = vz0 + x.dist;
-        const float rv2 = vx * vx + vy * vy;
-        const float d = sqrtf(rv2 + vz * vz);
-        int klo = (int)ceilf((d - kCellR - a.R0) / a.dR);
-        int khi = (int)floorf((d + kCellR - a.R0) / a.dR);
-        klo = max(klo, 0);
-        khi = min(khi, a.K - 1);
-        if (klo <= khi) {
-            const float rv = sqrtf(rv2);
-            const float thc = atan2f(rv, vz);
-            float phc = atan2f(vy, vx);
-            if (phc < 0.f) phc += kTwoPi;
-            const int cbase = x.cls * a.K;
-            for (int k = klo; k <= khi; ++k) {
-                const int nr = __ldg(a.t.ring_cnt + cbase + k);
-                if (nr <= 1) continue;
-                const float Rk = __ldg(a.t.Rk + k);
-                // half-angle of the cone through the shell-ball intersection: sin^2(gam/2)
-                const float dd = Rk - d;
-                const float s2 = (rc2 - dd * dd) / (4.f * Rk * d);
-                if (!(s2 > 0.f)) continue;
-                const float gam = s2 >= 1.f ? 3.14159265f : 2.f * asinf(sqrtf(s2));
-                const int ilo = max(1, (int)ceilf(Rk * (thc - gam) - 1e-3f));
-                const int ihi = min(nr - 1, (int)floorf(Rk * (thc + gam) + 1e-3f));
-                if (ilo > ihi) continue;
-                const float gp = gprime<DT>(a, q, k);
-                if (gp == 0.f) continue;
-                const int off = __ldg(a.t.ring_off + cbase + k);
-                for (int i = ilo; i <= ihi; ++i) {
-                    const Ring r = a.t.rings[off + i];
-                    if (r.nj == 0) continue;
-                    // distance from the cell centre to a ring point at azimuth phi:
-                    // dz^2 + (rv - a)^2 + 4 a rv sin^2((phi - phc)/2) <= rc^2
-                    const float dz = vz0 - r.h;
-                    const float dr = rv - r.a;
-                    const float rem = rc2 - dz * dz - dr * dr;
-                    if (!(rem > 0.f)) continue;
-                    int jlo0, jhi0;
-                    bool all = false;
-                    const float den = 4.f * r.a * rv;
-                    float delta = 0.f;
-                    if (!(den > 1e-12f) || rem >= den) all = true;
-                    else {
-                        delta = 2.f * asinf(sqrtf(rem / den)) + 2e-3f;
-                        if (delta >= 3.1f) all = true;
-                    }
-                    const float3 B = ring_base(a.O, x.ez, r.h);
-                    for (int sh = -1; sh <= 1; ++sh) {
-                        if (all) {
-                            if (sh != 0) continue;
-                            jlo0 = 0; jhi0 = r.nj - 1;
-                        } else {
-                            const float c0 = phc + sh * kTwoPi;
-                            jlo0 = max(0, (int)ceilf((c0 - delta) / r.dphi));
-                            jhi0 = min(r.nj - 1, (int)floorf((c0 + delta) / r.dphi));
-                        }
-                        for (int j = jlo0; j <= jhi0; ++j) {
-                            float u, v;
-                            ring_uv(r, j, u, v);
-                            const float3 P = ring_point(B, x.ex, x.ey, u, v);
-                            const float fx = floorf(P.x), fy = floorf(P.y), fz = floorf(P.z);
-                            if ((int)fx != mx || (int)fy != my || (int)fz != mz) continue;
-                            const float wx = P.x - fx, wy = P.y - fy, wz = P.z - fz;
-                            const float ux = 1.f - wx, uy = 1.f - wy, uz = 1.f - wz;
-                            const float g00 = gp * uz * uy, g01 = gp * uz * wy, g10 = gp * wz * uy, g11 = gp * wz * wy;
-                            acc[0] = fmaf(g00, ux, acc[0]); acc[1] = fmaf(g00, wx, acc[1]);
-                            acc[2] = fmaf(g01, ux, acc[2]); acc[3] = fmaf(g01, wx, acc[3]);
-                            acc[4] = fmaf(g10, ux, acc[4]); acc[5] = fmaf(g10, wx, acc[5]);
-                            acc[6] = fmaf(g11, ux, acc[6]); acc[7] = fmaf(g11, wx, acc[7]);
-                        }
+    for (int qp = q0; qp < q1; qp += a.qpass) {
+        const int qe = min(q1, qp + a.qpass);
+        const int units = (qe - qp) * a.kspan;
+        for (int u = warp; u < units; u += nwarps) {
+            const int q = qp + u / a.kspan;
+            const Xdcr &x = a.t.xd[q];
+            BrickView v;
+            brick_view(x, a.O, c, rb, a.R0, a.dR, a.K, v);
+            const int k = v.k0 + u % a.kspan;
+            if (k > v.k1) continue;
+            const int ck = v.cls * a.K + k;
+            const int nr = __ldg(a.t.ring_cnt + ck);
+            int ilo, ihi;
+            if (!shell_ring_range(v, __ldg(a.t.Rk + k), nr, rb2, ilo, ihi)) continue;
+            const float gq = gprime<DT>(a, q, k) * scale;
+            if (gq == 0.f) continue;
+            const int off = __ldg(a.t.ring_off + ck);
+            for (int i = ilo + sub; i <= ihi; i += kSubs) {
+                const Ring r = a.t.rings[off + i];
+                int a0, a1, b0, b1;
+                if (!ring_ranges(v, r, rb2, a0, a1, b0, b1)) continue;
+                const float3 Bq = ring_base(a.O, v.ez, r.h);
+                const int na = a1 - a0 + 1, nt = na + max(0, b1 - b0 + 1);
+                for (int t = sl; t < nt; t += kAdjLanesPerRing) {
+                    const int j = t < na ? a0 + t : b0 + (t - na);
+                    float uu, vv;
+                    ring_uv(r, j, uu, vv);
+                    const float3 P = ring_point(Bq, v.ex, v.ey, uu, vv);
+                    const float fx = floorf(P.x), fy = floorf(P.y), fz = floorf(P.z);
+                    const int lx = (int)fx - L[0], ly = (int)fy - L[1], lz = (int)fz - L[2];
+                    if ((unsigned)lx < (unsigned)E[0] && (unsigned)ly < (unsigned)E[1] && (unsigned)lz < (unsigned)E[2]) {
+                        const float wx = P.x - fx, wy = P.y - fy, wz = P.z - fz;
+                        const float ux = 1.f - wx, uy = 1.f - wy, uz = 1.f - wz;
+                        const float g00 = gq * uz * uy, g01 = gq * uz * wy, g10 = gq * wz * uy, g11 = gq * wz * wy;
+                        const int b = lz * S2 + ly * S1 + lx;
+                        sadd(shi, slo, b, g00 * ux);          sadd(shi, slo, b + 1, g00 * wx);
+                        sadd(shi, slo, b + S1, g01 * ux);     sadd(shi, slo, b + S1 + 1, g01 * wx);
+                        sadd(shi, slo, b + S2, g10 * ux);     sadd(shi, slo, b + S2 + 1, g10 * wx);
+                        sadd(shi, slo, b + S2 + S1, g11 * ux); sadd(shi, slo, b + S2 + S1 + 1, g11 * wx);
                     }
                 }
             }
         }
-        if ((q & 31) == 31) {
-#pragma unroll
-            for (int c = 0; c < 8; ++c) { outer[c] += acc[c]; acc[c] = 0.f; }
+        __syncthreads();
+        // fold the pass into the 64-bit volume accumulator (nodes on brick faces are shared
+        // with neighbouring bricks: integer atomics)
+        for (int idx = threadIdx.x; idx < NN; idx += blockDim.x) {
+            const int hi = shi[idx];
+            const unsigned int lo = slo[idx];
+            if (hi != 0 || lo != 0u) {
+                shi[idx] = 0; slo[idx] = 0u;
+                const int x = idx % S1 + L[0], y = (idx / S1) % S1 + L[1], z = idx / S2 + L[2];
+                if (x >= 0 && x < a.nx && y >= 0 && y < a.ny && z >= 0 && z < a.nz) {
+                    const long long v = (long long)hi * 32768LL + (long long)lo;
+                    atomicAdd(a.vacc + ((size_t)z * a.ny + y) * a.nx + x, (unsigned long long)v);
+                }
+            }
         }
+        __syncthreads();
     }
-    float4 *o = reinterpret_cast<float4 *>(a.part + (size_t)cell * 8);
-    o[0] = make_float4(a.ds2 * (outer[0] + acc[0]), a.ds2 * (outer[1] + acc[1]), a.ds2 * (outer[2] + acc[2]),
-                       a.ds2 * (outer[3] + acc[3]));
-    o[1] = make_float4(a.ds2 * (outer[4] + acc[4]), a.ds2 * (outer[5] + acc[5]), a.ds2 * (outer[6] + acc[6]),
-                       a.ds2 * (outer[7] + acc[7]));
 }
 
-// node n = sum over its eight cells m = n - c of corner c of m; corner index (dz, dy, dx) bits.
-__global__ void k_combine(const float *__restrict__ part, float *__restrict__ vol, int nx, int ny, int nz) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= nx * ny * nz) return;
-    const int ix = n % nx, iy = (n / nx) % ny, iz = n / (nx * ny);
-    const int cx = nx + 1, cy = ny + 1;
-    float s = 0.f;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
-        const int m = ((iz - dz + 1) * cy + (iy - dy + 1)) * cx + (ix - dx + 1);
-        s += __ldg(part + (size_t)m * 8 + c);
-    }
-    vol[n] = s;
+__global__ void k_finish_t(const long long *__restrict__ vacc, float *__restrict__ vol, size_t n,
+                           const unsigned int *amax, float gscale, double ds2) {
+    const double unit = ds2 / pow2_scale((double)__uint_as_float(*amax) * (double)gscale, 30);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        vol[i] = (float)((double)vacc[i] * unit);
 }
 
 int launch_backproject(Plan &p, const void *data, float *vol, cudaStream_t s) {
+    const size_t N = (size_t)p.nx * p.ny * p.nz, M = (size_t)p.Q * p.K;
+    cudaError_t e = cudaMemsetAsync(p.d_amax + 1, 0, sizeof(unsigned int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.d_vacc, 0, sizeof(long long) * N, s);
+    if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_backproject: memset: ") + cudaGetErrorString(e));
+    k_absmax<<<(unsigned)std::min<size_t>((M + 255) / 256, 152 * 8), 256, 0, s>>>(data, M, p.g.data_dtype, p.d_amax + 1);
     AdjArgs a;
-    a.t = p.t; a.y = data; a.part = p.d_part;
+    a.t = p.t; a.y = data;
+    a.vacc = (unsigned long long *)p.d_vacc;
+    a.amax = p.d_amax + 1;
     a.nx = p.nx; a.ny = p.ny; a.nz = p.nz; a.K = p.K; a.Q = p.Q;
-    for (int d = 0; d < 3; ++d) a.O[d] = p.O[d];
-    a.R0 = p.R0; a.dR = p.dR; a.ds2 = p.ds2; a.apply_d = p.g.apply_d;
-    const long long cells = (long long)(p.nx + 1) * (p.ny + 1) * (p.nz + 1);
-    const unsigned blocks = (unsigned)((cells + 127) / 128);
+    for (int d = 0; d < 3; ++d) { a.nb[d] = p.adj.nb[d]; a.bs[d] = p.adj.bs[d]; a.O[d] = p.O[d]; }
+    a.qchunk = p.adj.qchunk; a.kspan = p.adj.kspan; a.qpass = p.adj_qpass;
+    a.R0 = p.R0; a.dR = p.dR;
+    a.gscale = p.gscale;
+    a.apply_d = p.g.apply_d;
     const bool prof = p.profiling && p.ev_used[1] + 2 <= (int)p.ev[1].size();
     if (prof) cudaEventRecord(p.ev[1][p.ev_used[1]], s);
+    const unsigned grid = (unsigned)p.adj.items;
     switch (p.g.data_dtype) {
-        case OAT_F32: k_cell_gather<OAT_F32><<<blocks, 128, 0, s>>>(a); break;
-        case OAT_F16: k_cell_gather<OAT_F16><<<blocks, 128, 0, s>>>(a); break;
-        default: k_cell_gather<OAT_BF16><<<blocks, 128, 0, s>>>(a); break;
+        case OAT_F32: k_brick_gather_t<kBA, OAT_F32><<<grid, kAdjThreads, p.adj.smem, s>>>(a); break;
+        case OAT_F16: k_brick_gather_t<kBA, OAT_F16><<<grid, kAdjThreads, p.adj.smem, s>>>(a); break;
+        default: k_brick_gather_t<kBA, OAT_BF16><<<grid, kAdjThreads, p.adj.smem, s>>>(a); break;
     }
     if (prof) { cudaEventRecord(p.ev[1][p.ev_used[1] + 1], s); p.ev_used[1] += 2; }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_backproject: k_cell_gather: ") + cudaGetErrorString(e));
-    const long long N = (long long)p.nx * p.ny * p.nz;
-    k_combine<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(p.d_part, vol, p.nx, p.ny, p.nz);
     e = cudaGetLastError();
-    if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_backproject: k_combine: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_backproject: k_brick_gather_t: ") + cudaGetErrorString(e));
+    k_finish_t<<<(unsigned)std::min<size_t>((N + 255) / 256, 152 * 16), 256, 0, s>>>(
+        (const long long *)p.d_vacc, vol, N, p.d_amax + 1, p.gscale, p.g.spacing_mm * p.g.spacing_mm);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_backproject: k_finish_t: ") + cudaGetErrorString(e));
     return OAT_OK;
+}
+
+int set_adjoint_attributes() {
+    const int bytes = (int)(2 * sizeof(int) * (kBA + 1) * (kBA + 1) * (kBA + 1));
+    cudaError_t e = cudaFuncSetAttribute(k_brick_gather_t<kBA, OAT_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_brick_gather_t<kBA, OAT_F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_brick_gather_t<kBA, OAT_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e == cudaSuccess ? OAT_OK : set_error(OAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
 }
 
 }  // namespace oat

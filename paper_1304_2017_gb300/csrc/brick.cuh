@@ -1,0 +1,113 @@
+// Brick enumeration shared by the projector and the backprojector.
+//
+// The cell range [-1, n-1]^3 (cell m = [m, m+1)^3 in grid-index units; cells -1 and n-1 hold
+// the points whose stencil is half outside the grid) is tiled by bricks of B^3 cells.  A
+// lattice point belongs to the brick containing floor(P).  For one brick and one transducer
+// the lattice points that can lie in the brick are found through the brick's bounding sphere
+// (centre c, radius rb):
+//   shells   |rho_k - |c - r_q|| <= rb                                (triangle inequality)
+//   rings    |theta_i - theta_c| <= gamma_k, the half-angle of the cone through the circle in
+//            which shell k cuts the sphere
+//   points   the azimuth window in which the ring is within rb of c (exact point-to-ring
+//            distance); up to two index ranges because phi wraps at 2 pi.
+// All windows carry a small margin; every candidate is then tested exactly with floor(P), so
+// the windows only need to be conservative.
+#pragma once
+
+#include "oat_internal.h"
+
+namespace oat {
+
+constexpr float kTwoPiF = 6.28318530717958647692f;
+
+// Brick seen from one transducer (local frame of the transducer, index units).
+struct BrickView {
+    float ex[3], ey[3], ez[3];
+    float wz0;     // (c - O) . e_z : axial coordinate of the centre about the global origin
+    float rw;      // distance of the centre from the transducer axis
+    float d;       // distance of the centre from the transducer
+    float thc;     // polar angle of the centre (from e_z)
+    float phc;     // azimuth of the centre in [0, 2 pi)
+    int cls, k0, k1;
+};
+
+__device__ __forceinline__ void brick_view(const Xdcr &x, const float O[3], const float c[3], float rb, float R0,
+                                           float dR, int K, BrickView &v) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) { v.ex[d] = x.ex[d]; v.ey[d] = x.ey[d]; v.ez[d] = x.ez[d]; }
+    const float c0 = c[0] - O[0], c1 = c[1] - O[1], c2 = c[2] - O[2];
+    const float vx = c0 * x.ex[0] + c1 * x.ex[1] + c2 * x.ex[2];
+    const float vy = c0 * x.ey[0] + c1 * x.ey[1] + c2 * x.ey[2];
+    v.wz0 = c0 * x.ez[0] + c1 * x.ez[1] + c2 * x.ez[2];
+    const float vz = v.wz0 + x.dist;
+    const float rw2 = vx * vx + vy * vy;
+    v.rw = sqrtf(rw2);
+    v.d = sqrtf(rw2 + vz * vz);
+    v.k0 = max(0, (int)ceilf((v.d - rb - R0) / dR));
+    v.k1 = min(K - 1, (int)floorf((v.d + rb - R0) / dR));
+    v.thc = atan2f(v.rw, vz);
+    float ph = atan2f(vy, vx);
+    v.phc = ph < 0.f ? ph + kTwoPiF : ph;
+    v.cls = x.cls;
+}
+
+// Rings of shell k (radius Rk, nr rings) that can meet the bounding sphere.
+__device__ __forceinline__ bool shell_ring_range(const BrickView &v, float Rk, int nr, float rb2, int &ilo, int &ihi) {
+    if (nr <= 1) return false;
+    const float dd = Rk - v.d;
+    const float s2 = (rb2 - dd * dd) / (4.f * Rk * v.d);   // sin^2(gamma / 2)
+    if (!(s2 > 0.f)) return false;
+    const float gam = s2 >= 1.f ? 3.14159265f : 2.f * asinf(sqrtf(s2));
+    ilo = max(1, (int)ceilf(Rk * (v.thc - gam) - 0.01f));
+    ihi = min(nr - 1, (int)floorf(Rk * (v.thc + gam) + 0.01f));
+    return ilo <= ihi;
+}
+
+// Azimuth index ranges of ring r within rb of the centre: [a0, a1] and [b0, b1] (either may
+// be empty, i.e. lo > hi).  Returns false when the ring misses the sphere.
+__device__ __forceinline__ bool ring_ranges(const BrickView &v, const Ring &r, float rb2, int &a0, int &a1, int &b0,
+                                            int &b1) {
+    a0 = 0; a1 = -1; b0 = 0; b1 = -1;
+    if (r.nj == 0) return false;
+    const float dz = v.wz0 - r.h;
+    const float dr = v.rw - r.a;
+    const float rem = rb2 - dz * dz - dr * dr;
+    if (!(rem > 0.f)) return false;
+    const float den = 4.f * r.a * v.rw;
+    if (!(den > 1e-12f) || rem >= den) { a1 = r.nj - 1; return true; }
+    const float delta = 2.f * asinf(sqrtf(rem / den)) + 2e-3f;
+    if (delta >= 3.1f) { a1 = r.nj - 1; return true; }
+    const float inv = 1.f / r.dphi;
+    a0 = max(0, (int)ceilf((v.phc - delta) * inv));
+    a1 = min(r.nj - 1, (int)floorf((v.phc + delta) * inv));
+    if (v.phc - delta < 0.f) {          // window wraps below 0: points near 2 pi
+        b0 = max(0, (int)ceilf((v.phc - delta + kTwoPiF) * inv));
+        b1 = r.nj - 1;
+    } else if (v.phc + delta >= kTwoPiF) {   // wraps above 2 pi: points near 0
+        b0 = 0;
+        b1 = min(r.nj - 1, (int)floorf((v.phc + delta - kTwoPiF) * inv));
+    }
+    return true;
+}
+
+// Lowest cell L and cell counts E (<= bs) of brick id in a grid of nb[3] bricks (x fastest)
+// tiling the cells [-1, n-1] of each axis.
+__device__ __forceinline__ void brick_box(int id, const int nb[3], const int bs[3], const int n[3], int L[3], int E[3]) {
+    const int b[3] = {id % nb[0], (id / nb[0]) % nb[1], id / (nb[0] * nb[1])};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        L[d] = -1 + bs[d] * b[d];
+        E[d] = min(bs[d], n[d] - L[d]);
+    }
+}
+
+// Power-of-two scale 2^e with |x * 2^e| <= 2^bits for every |x| <= bound (1 if bound is zero or
+// not finite).  Sums are accumulated as integers in this fixed-point unit: integer addition is
+// exact and associative, so the result does not depend on the order of the contributions.
+__host__ __device__ __forceinline__ double pow2_scale(double bound, int bits) {
+    if (!(bound > 0.0) || !(bound < 1e300)) return 1.0;
+    int e = bits - (int)ceil(log2(bound));
+    return ldexp(1.0, e);
+}
+
+}  // namespace oat

@@ -49,6 +49,19 @@ struct DevTables {
     const double *wD64;       // [K] the same in double (forward D)
 };
 
+// Brick tiling of the cell range [-1, n-1]^3 for one direction: nb bricks per axis of bs cells
+// (bs <= the kernel's compile-time brick edge), work items = bricks x transducer chunks.
+struct BrickCfg {
+    int nb[3] = {1, 1, 1};
+    int bs[3] = {1, 1, 1};
+    int qchunk = 1;
+    int kspan = 1;          // upper bound of the shells crossing one brick
+    long long items = 0;
+    size_t smem = 0;
+};
+
+constexpr int kBA = 24;     // backprojector brick edge: (kBA+1)^3 pairs of 32-bit node-sum halves in shared memory
+
 struct Plan {
     oat_geometry g{};
     std::vector<double> pos;
@@ -60,14 +73,22 @@ struct Plan {
     float ds2 = 0;               // Delta_s^2
     float R0 = 0, dR = 0;        // rho_0 / Delta_s and c dt / Delta_s
     long long n_rings = 0, points_ball = 0, n_items = 0;
+    long long max_shell_points = 0;   // largest N_i-ring lattice of one shell (fixed-point bound)
+    float gscale = 1.f;               // max |g'| / max |y|: 2 max_k C_D/tau_k with D, 1 without
+    int adj_qpass = 1;                // transducers per backprojector pass (bounds the 32-bit halves)
+    BrickCfg adj;                      // backprojector brick tiling
+    const int4 *d_ritems = nullptr;    // radial work items (class, first shell, first in qlist, count)
+    long long n_ritems = 0;
     long long table_bytes = 0, scratch_bytes = 0;
     std::vector<long long> cls_points;   // [n_cls * K] points per (class, k)
 
     // device memory
     void *d_tables = nullptr;   // one allocation holding every table
     DevTables t{};
-    double *d_g = nullptr;      // [Q][K] scratch: G alpha (FP64 sum of the compensated FP32 pair)
-    float *d_part = nullptr;    // [(nx+1)(ny+1)(nz+1)][8] scratch: per-cell corner sums of G^T
+    long long *d_gacc = nullptr;     // [Q][K] scratch: fixed-point sums of G alpha
+    long long *d_vacc = nullptr;     // [nz][ny][nx] scratch: fixed-point node sums of G^T g'
+    unsigned int *d_amax = nullptr;  // [2] scratch: max|alpha| and max|y| bit patterns
+    unsigned long long *d_count = nullptr;  // point counter of oat_plan_query
 
     // profiling
     bool profiling = false;
@@ -84,6 +105,7 @@ int set_error(int code, const std::string &msg);
 int launch_project(Plan &p, const float *vol, void *data, cudaStream_t s);
 int launch_backproject(Plan &p, const void *data, float *vol, cudaStream_t s);
 int count_grid_points(Plan &p, long long *out);
+int set_adjoint_attributes();
 
 constexpr int kMaxEvents = 4096;
 

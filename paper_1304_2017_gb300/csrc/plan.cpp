@@ -198,6 +198,67 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
         return set_error(OAT_ERR_UNSUPPORTED, "oat_plan_create: too many work items");
     }
 
+    p->max_shell_points = 0;
+    for (long long np : p->cls_points) p->max_shell_points = std::max(p->max_shell_points, np);
+
+    // brick tilings of the cells [-1, n-1] for the two directions
+    auto tile = [&](BrickCfg &bc, int B, size_t node_bytes) {
+        const int n[3] = {p->nx, p->ny, p->nz};
+        long long bricks = 1;
+        double diag2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            bc.nb[d] = (n[d] + 1 + B - 1) / B;
+            bc.bs[d] = (n[d] + 1 + bc.nb[d] - 1) / bc.nb[d];
+            while (bc.nb[d] > 1 && bc.bs[d] * (bc.nb[d] - 1) >= n[d] + 1) --bc.nb[d];   // no empty brick
+            bricks *= bc.nb[d];
+            diag2 += (double)bc.bs[d] * bc.bs[d];
+        }
+        const double rb = 0.5 * std::sqrt(diag2) + 0.05;
+        bc.kspan = (int)std::ceil(2.0 * rb / (g.c_mm_per_us * p->dt / ds)) + 2;
+        const long long target = 152LL * 8;
+        long long chunks = std::max(1LL, std::min<long long>(Q, (target + bricks - 1) / bricks));
+        bc.qchunk = (int)((Q + chunks - 1) / chunks);
+        bc.items = bricks * ((Q + bc.qchunk - 1) / bc.qchunk);
+        bc.smem = node_bytes * (size_t)(B + 1) * (B + 1) * (B + 1);
+    };
+    tile(p->adj, kBA, 2 * sizeof(int));
+    {
+        // contributions one transducer adds to one node: 8 cells x (shells crossing a cell:
+        // diameter sqrt(3) over the shell spacing, + 2) x (2 rings x 3 points, + margin)
+        const double dRs = g.c_mm_per_us * p->dt / ds;
+        const long long shells = (long long)std::floor(std::sqrt(3.0) / dRs) + 2;
+        const long long per_q = 8 * shells * 9;
+        p->adj_qpass = (int)std::max<long long>(1, std::min<long long>(Q, 32768 / per_q));
+        if (per_q > 32768) {
+            delete p;
+            return set_error(OAT_ERR_UNSUPPORTED, "oat_plan_create: shells too dense for the backprojector's "
+                                                  "fixed-point accumulation (c dt / spacing too small)");
+        }
+    }
+
+    // radial-lane work items: (class, block of 32 shells, tile of 8 transducers), heaviest first
+    std::vector<int4> ritems;
+    std::vector<long long> rwork;
+    for (int c = 0; c < C; ++c)
+        for (int kb = 0; kb < K; kb += 32) {
+            long long w = 0;
+            for (int k = kb; k < std::min(K, kb + 32); ++k) w += p->cls_points[(size_t)c * K + k];
+            if (w == 0) continue;
+            for (int s0 = 0; s0 < cls_n[c]; s0 += kTileQ) {
+                ritems.push_back(make_int4(c, kb, cls_start[c] + s0, std::min(kTileQ, cls_n[c] - s0)));
+                rwork.push_back(w);
+            }
+        }
+    {
+        std::vector<size_t> ord(ritems.size());
+        for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
+        std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) { return rwork[x] > rwork[y]; });
+        std::vector<int4> sorted(ritems.size());
+        for (size_t i = 0; i < ord.size(); ++i) sorted[i] = ritems[ord[i]];
+        ritems.swap(sorted);
+    }
+    p->n_ritems = (long long)ritems.size();
+
     std::vector<float> Rk(K), wD(K);
     std::vector<double> wD64(K);
     for (int k = 0; k < K; ++k) {
@@ -207,12 +268,16 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
         wD[k] = tau > 0.0 ? (float)(p->cd / tau) : 0.f;
         wD64[k] = tau > 0.0 ? p->cd / tau : 0.0;
     }
+    double wmax = 0.0;
+    for (int k = 0; k < K; ++k) wmax = std::max(wmax, (double)wD[k]);
+    p->gscale = g.apply_d ? (float)(2.0 * wmax * (1.0 + 1e-6)) : 1.f;
 
     // one device blob for every table
     std::vector<unsigned char> blob;
     size_t o_rings = push_bytes(blob, rings), o_off = push_bytes(blob, ring_off), o_cnt = push_bytes(blob, ring_cnt);
     size_t o_xd = push_bytes(blob, xd), o_ql = push_bytes(blob, qlist), o_it = push_bytes(blob, items);
     size_t o_rk = push_bytes(blob, Rk), o_wd = push_bytes(blob, wD), o_wd64 = push_bytes(blob, wD64);
+    size_t o_ri = push_bytes(blob, ritems);
     p->table_bytes = (long long)blob.size();
 
     int prev = 0;
@@ -225,8 +290,9 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
     auto fail = [&](cudaError_t err, const char *what) {
         int code = (err == cudaErrorMemoryAllocation) ? OAT_ERR_OOM : OAT_ERR_CUDA;
         if (p->d_tables) cudaFree(p->d_tables);
-        if (p->d_g) cudaFree(p->d_g);
-        if (p->d_part) cudaFree(p->d_part);
+        if (p->d_gacc) cudaFree(p->d_gacc);
+        if (p->d_vacc) cudaFree(p->d_vacc);
+        if (p->d_amax) cudaFree(p->d_amax);
         delete p;
         cudaGetLastError();
         cudaSetDevice(prev);
@@ -235,11 +301,18 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
     if ((e = cudaMalloc(&p->d_tables, blob.size())) != cudaSuccess) return fail(e, "cudaMalloc(tables)");
     if ((e = cudaMemcpy(p->d_tables, blob.data(), blob.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
         return fail(e, "cudaMemcpy(tables)");
-    size_t g_bytes = sizeof(double) * (size_t)Q * K;
-    size_t part_bytes = sizeof(float) * 8 * (size_t)(p->nx + 1) * (p->ny + 1) * (p->nz + 1);
-    if ((e = cudaMalloc(&p->d_g, g_bytes)) != cudaSuccess) return fail(e, "cudaMalloc(g scratch)");
-    if ((e = cudaMalloc(&p->d_part, part_bytes)) != cudaSuccess) return fail(e, "cudaMalloc(G^T scratch)");
-    p->scratch_bytes = (long long)(g_bytes + part_bytes);
+    size_t g_bytes = sizeof(long long) * (size_t)Q * K;
+    size_t v_bytes = sizeof(long long) * (size_t)p->nx * p->ny * p->nz;
+    if ((e = cudaMalloc(&p->d_gacc, g_bytes)) != cudaSuccess) return fail(e, "cudaMalloc(G scratch)");
+    if ((e = cudaMalloc(&p->d_vacc, v_bytes)) != cudaSuccess) return fail(e, "cudaMalloc(G^T scratch)");
+    if ((e = cudaMalloc(&p->d_amax, 256)) != cudaSuccess) return fail(e, "cudaMalloc(scale scratch)");
+    p->d_count = (unsigned long long *)((char *)p->d_amax + 128);
+    p->scratch_bytes = (long long)(g_bytes + v_bytes + 256);
+    if (set_adjoint_attributes() != OAT_OK) {
+        std::string msg = std::string("oat_plan_create: ") + oat_last_error();
+        fail(cudaSuccess, "kernel attributes");
+        return set_error(OAT_ERR_CUDA, msg);
+    }
     cudaSetDevice(prev);
 
     unsigned char *base = (unsigned char *)p->d_tables;
@@ -252,6 +325,7 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
     p->t.Rk = (const float *)(base + o_rk);
     p->t.wD = (const float *)(base + o_wd);
     p->t.wD64 = (const double *)(base + o_wd64);
+    p->d_ritems = (const int4 *)(base + o_ri);
     *out = p;
     return OAT_OK;
 }
@@ -264,8 +338,9 @@ void plan_destroy(Plan *p) {
     for (int w = 0; w < 2; ++w)
         for (cudaEvent_t e : p->ev[w]) cudaEventDestroy(e);
     if (p->d_tables) cudaFree(p->d_tables);
-    if (p->d_g) cudaFree(p->d_g);
-    if (p->d_part) cudaFree(p->d_part);
+    if (p->d_gacc) cudaFree(p->d_gacc);
+    if (p->d_vacc) cudaFree(p->d_vacc);
+    if (p->d_amax) cudaFree(p->d_amax);
     cudaSetDevice(prev);
     delete p;
 }

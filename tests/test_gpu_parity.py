@@ -158,3 +158,21 @@ def test_repeat_calls_deterministic_and_stream(oat, torch_cuda):
     s.synchronize()
     assert torch.equal(u1, u2) and torch.equal(a1, a2)
     plan.close()
+
+
+def test_plan_reuse_after_other_inputs(oat, torch_cuda):
+    """A plan reused with new inputs (including shells that hold no lattice point, whose
+    sums no work item writes) gives the oracle's result for the new inputs."""
+    torch = torch_cuda
+    geom = CASES["partial_window"]()
+    plan = oat.Plan(geom)
+    a1 = W.random_volume(geom, seed=21) * 10
+    a2 = W.spheres_phantom(geom, 3, seed=22)
+    y1 = W.random_data(geom, seed=23) * 5
+    y2 = W.random_data(geom, seed=24)
+    plan.project(torch.from_numpy(a1).cuda()); plan.backproject(torch.from_numpy(y1).cuda())
+    u = plan.project(torch.from_numpy(a2).cuda()).cpu().numpy()
+    a = plan.backproject(torch.from_numpy(y2).cuda()).cpu().numpy()
+    assert rel(u, oracle.H(geom, a2)) <= TOL
+    assert rel(a, oracle.Ht(geom, y2)) <= TOL
+    plan.close()
