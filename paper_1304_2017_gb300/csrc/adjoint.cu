@@ -24,8 +24,7 @@
 
 namespace oat {
 
-constexpr int kAdjThreads = 512;
-constexpr int kAdjLanesPerRing = 16;
+constexpr int kAdjThreads = 1024;
 
 __global__ void k_absmax(const void *__restrict__ x, size_t n, int dtype, unsigned int *out);
 
@@ -75,11 +74,39 @@ __device__ __forceinline__ void sadd(int *hi, unsigned int *lo, int idx, float x
     }
 }
 
+// Ring record of the flattened candidate list of one warp: ring centre, radius, azimuth step,
+// its index ranges [ja, ja + na) and [jb, ...), and the ring's first position in the list.
+struct RingSlot {
+    float cx, cy, cz, a;
+    float dphi;
+    int ja, na, jb;
+    int start;
+    int pad[3];
+};
+
+constexpr int kQueue = 64;   // per-warp queue of owned points (power of two, >= 63)
+
+// Scatter one owned point (cell-local weights wx, wy, wz; first node b) with value gq.
+template <int S1, int S2>
+__device__ __forceinline__ void scatter8(int *shi, unsigned int *slo, float4 e, float gq) {
+    const float wx = e.x, wy = e.y, wz = e.z;
+    const int b = __float_as_int(e.w);
+    const float ux = 1.f - wx, uy = 1.f - wy, uz = 1.f - wz;
+    const float g00 = gq * uz * uy, g01 = gq * uz * wy, g10 = gq * wz * uy, g11 = gq * wz * wy;
+    sadd(shi, slo, b, g00 * ux);           sadd(shi, slo, b + 1, g00 * wx);
+    sadd(shi, slo, b + S1, g01 * ux);      sadd(shi, slo, b + S1 + 1, g01 * wx);
+    sadd(shi, slo, b + S2, g10 * ux);      sadd(shi, slo, b + S2 + 1, g10 * wx);
+    sadd(shi, slo, b + S2 + S1, g11 * ux); sadd(shi, slo, b + S2 + S1 + 1, g11 * wx);
+}
+
 template <int B, int DT>
 __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
-    extern __shared__ int shi[];   // (B+1)^3 high halves, then (B+1)^3 low halves
+    extern __shared__ int shi[];   // (B+1)^3 high halves, (B+1)^3 low halves, ring slots, queues
     constexpr int S1 = B + 1, S2 = (B + 1) * (B + 1), NN = (B + 1) * (B + 1) * (B + 1);
+    constexpr int NN2 = 2 * NN + ((2 * NN) & 3 ? 4 - ((2 * NN) & 3) : 0);
     unsigned int *slo = (unsigned int *)(shi + NN);
+    RingSlot *slots = (RingSlot *)(shi + NN2);
+    float4 *queues = (float4 *)(slots + kAdjThreads);
     const int nqc = (a.Q + a.qchunk - 1) / a.qchunk;
     const int brick = blockIdx.x / nqc;
     const int q0 = (blockIdx.x % nqc) * a.qchunk;
@@ -92,24 +119,27 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
     for (int idx = threadIdx.x; idx < NN; idx += blockDim.x) { shi[idx] = 0; slo[idx] = 0u; }
     __syncthreads();
 
-    // bounding sphere of the brick's cells [L, L + E)
+    // bounding sphere and box of the brick's cells [L, L + E)
     const float c[3] = {L[0] + 0.5f * E[0], L[1] + 0.5f * E[1], L[2] + 0.5f * E[2]};
+    const float blo[3] = {(float)L[0], (float)L[1], (float)L[2]};
+    const float bhi[3] = {(float)(L[0] + E[0]), (float)(L[1] + E[1]), (float)(L[2] + E[2])};
     const float rb = 0.5f * sqrtf((float)(E[0] * E[0] + E[1] * E[1] + E[2] * E[2])) + 0.05f;
     const float rb2 = rb * rb;
     // contributions |w g'| <= max|g'| map to at most 2^30 units
     const float scale = (float)pow2_scale((double)__uint_as_float(*a.amax) * (double)a.gscale, 30);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int sub = lane / kAdjLanesPerRing, sl = lane % kAdjLanesPerRing;
-    constexpr int kSubs = 32 / kAdjLanesPerRing;
+    RingSlot *ws = slots + warp * 32;
+    float4 *wq = queues + warp * kQueue;
+    const unsigned lt_mask = (1u << lane) - 1u;
 
     for (int qp = q0; qp < q1; qp += a.qpass) {
         const int qe = min(q1, qp + a.qpass);
         const int units = (qe - qp) * a.kspan;
+        int vq = -1;
+        BrickView v;
         for (int u = warp; u < units; u += nwarps) {
             const int q = qp + u / a.kspan;
-            const Xdcr &x = a.t.xd[q];
-            BrickView v;
-            brick_view(x, a.O, c, rb, a.R0, a.dR, a.K, v);
+            if (q != vq) { brick_view(a.t.xd[q], a.O, c, rb, a.R0, a.dR, a.K, v); vq = q; }
             const int k = v.k0 + u % a.kspan;
             if (k > v.k1) continue;
             const int ck = v.cls * a.K + k;
@@ -119,31 +149,73 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
             const float gq = gprime<DT>(a, q, k) * scale;
             if (gq == 0.f) continue;
             const int off = __ldg(a.t.ring_off + ck);
-            for (int i = ilo + sub; i <= ihi; i += kSubs) {
-                const Ring r = a.t.rings[off + i];
-                int a0, a1, b0, b1;
-                if (!ring_ranges(v, r, rb2, a0, a1, b0, b1)) continue;
-                const float3 Bq = ring_base(a.O, v.ez, r.h);
-                const int na = a1 - a0 + 1, nt = na + max(0, b1 - b0 + 1);
-                for (int t = sl; t < nt; t += kAdjLanesPerRing) {
-                    const int j = t < na ? a0 + t : b0 + (t - na);
-                    float uu, vv;
-                    ring_uv(r, j, uu, vv);
-                    const float3 P = ring_point(Bq, v.ex, v.ey, uu, vv);
-                    const float fx = floorf(P.x), fy = floorf(P.y), fz = floorf(P.z);
-                    const int lx = (int)fx - L[0], ly = (int)fy - L[1], lz = (int)fz - L[2];
-                    if ((unsigned)lx < (unsigned)E[0] && (unsigned)ly < (unsigned)E[1] && (unsigned)lz < (unsigned)E[2]) {
-                        const float wx = P.x - fx, wy = P.y - fy, wz = P.z - fz;
-                        const float ux = 1.f - wx, uy = 1.f - wy, uz = 1.f - wz;
-                        const float g00 = gq * uz * uy, g01 = gq * uz * wy, g10 = gq * wz * uy, g11 = gq * wz * wy;
-                        const int b = lz * S2 + ly * S1 + lx;
-                        sadd(shi, slo, b, g00 * ux);          sadd(shi, slo, b + 1, g00 * wx);
-                        sadd(shi, slo, b + S1, g01 * ux);     sadd(shi, slo, b + S1 + 1, g01 * wx);
-                        sadd(shi, slo, b + S2, g10 * ux);     sadd(shi, slo, b + S2 + 1, g10 * wx);
-                        sadd(shi, slo, b + S2 + S1, g11 * ux); sadd(shi, slo, b + S2 + S1 + 1, g11 * wx);
+            int qh = 0, qt = 0;   // queue head and tail (warp-uniform)
+            for (int ib = ilo; ib <= ihi; ib += 32) {
+                // one lane per ring: azimuth windows clipped to the brick
+                const int i = ib + lane;
+                int a0 = 0, a1 = -1, b0 = 0, b1 = -1;
+                Ring r;
+                r.h = 0.f; r.a = 0.f; r.dphi = 0.f; r.nj = 0;
+                float3 Bq = make_float3(0.f, 0.f, 0.f);
+                if (i <= ihi) {
+                    r = a.t.rings[off + i];
+                    Bq = ring_base(a.O, v.ez, r.h);
+                    ring_box_ranges(v, r, Bq, rb2, blo, bhi, a0, a1, b0, b1);
+                }
+                const int na = max(0, a1 - a0 + 1), nb = max(0, b1 - b0 + 1), n = na + nb;
+                const unsigned ne = __ballot_sync(0xffffffffu, n > 0);
+                if (ne == 0u) continue;
+                int incl = n;   // inclusive prefix over lanes
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                if (n > 0) {
+                    RingSlot &sl = ws[__popc(ne & lt_mask)];
+                    sl.cx = Bq.x; sl.cy = Bq.y; sl.cz = Bq.z; sl.a = r.a;
+                    sl.dphi = r.dphi; sl.ja = a0; sl.na = na; sl.jb = b0; sl.start = incl - n;
+                }
+                __syncwarp();
+                const int nre = __popc(ne);
+                const int my_start = lane < nre ? ws[lane].start : 0x7fffffff;
+                // the warp's candidates, flattened: candidate f + lane belongs to the ring slot
+                // counted by the ring starts at or before it
+                for (int f = 0; f < total; f += 32) {
+                    const int before = __popc(__ballot_sync(0xffffffffu, my_start <= f));
+                    const unsigned inside = __reduce_or_sync(
+                        0xffffffffu, (my_start > f && my_start < f + 32) ? (1u << (my_start - f)) : 0u);
+                    const int cidx = f + lane;
+                    bool own = false;
+                    float4 ent;
+                    if (cidx < total) {
+                        const int si = before - 1 + __popc(inside & ((2u << lane) - 1u));
+                        const RingSlot sl = ws[si];
+                        const int o2 = cidx - sl.start;
+                        const int j = o2 < sl.na ? sl.ja + o2 : sl.jb + (o2 - sl.na);
+                        float uu, vv;
+                        ring_uv(sl.a, sl.dphi, j, uu, vv);
+                        const float3 P = ring_point(make_float3(sl.cx, sl.cy, sl.cz), v.ex, v.ey, uu, vv);
+                        const float fx = floorf(P.x), fy = floorf(P.y), fz = floorf(P.z);
+                        const int lx = (int)fx - L[0], ly = (int)fy - L[1], lz = (int)fz - L[2];
+                        own = (unsigned)lx < (unsigned)E[0] && (unsigned)ly < (unsigned)E[1] && (unsigned)lz < (unsigned)E[2];
+                        ent = make_float4(P.x - fx, P.y - fy, P.z - fz, __int_as_float(lz * S2 + ly * S1 + lx));
+                    }
+                    // queue the owned points; scatter them 32 at a time with every lane busy
+                    const unsigned om = __ballot_sync(0xffffffffu, own);
+                    if (own) wq[(qt + __popc(om & lt_mask)) & (kQueue - 1)] = ent;
+                    qt += __popc(om);
+                    __syncwarp();
+                    if (qt - qh >= 32) {
+                        scatter8<S1, S2>(shi, slo, wq[(qh + lane) & (kQueue - 1)], gq);
+                        qh += 32;
+                        __syncwarp();
                     }
                 }
+                __syncwarp();
             }
+            if (lane < qt - qh) scatter8<S1, S2>(shi, slo, wq[(qh + lane) & (kQueue - 1)], gq);
+            __syncwarp();
         }
         __syncthreads();
         // fold the pass into the 64-bit volume accumulator (nodes on brick faces are shared
@@ -155,8 +227,8 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
                 shi[idx] = 0; slo[idx] = 0u;
                 const int x = idx % S1 + L[0], y = (idx / S1) % S1 + L[1], z = idx / S2 + L[2];
                 if (x >= 0 && x < a.nx && y >= 0 && y < a.ny && z >= 0 && z < a.nz) {
-                    const long long v = (long long)hi * 32768LL + (long long)lo;
-                    atomicAdd(a.vacc + ((size_t)z * a.ny + y) * a.nx + x, (unsigned long long)v);
+                    const long long vv = (long long)hi * 32768LL + (long long)lo;
+                    atomicAdd(a.vacc + ((size_t)z * a.ny + y) * a.nx + x, (unsigned long long)vv);
                 }
             }
         }
@@ -205,8 +277,14 @@ int launch_backproject(Plan &p, const void *data, float *vol, cudaStream_t s) {
     return OAT_OK;
 }
 
+size_t adjoint_smem_bytes() {
+    const size_t nn2 = 2 * (size_t)(kBA + 1) * (kBA + 1) * (kBA + 1);
+    const size_t pad = (nn2 & 3) ? 4 - (nn2 & 3) : 0;
+    return sizeof(int) * (nn2 + pad) + sizeof(RingSlot) * kAdjThreads + sizeof(float4) * kQueue * (kAdjThreads / 32);
+}
+
 int set_adjoint_attributes() {
-    const int bytes = (int)(2 * sizeof(int) * (kBA + 1) * (kBA + 1) * (kBA + 1));
+    const int bytes = (int)adjoint_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(k_brick_gather_t<kBA, OAT_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_brick_gather_t<kBA, OAT_F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_brick_gather_t<kBA, OAT_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);

@@ -28,6 +28,8 @@ struct BrickView {
     float d;       // distance of the centre from the transducer
     float thc;     // polar angle of the centre (from e_z)
     float phc;     // azimuth of the centre in [0, 2 pi)
+    float m[3];    // |(e_x[d], e_y[d])|: a ring of radius a moves coordinate d by a m[d] cos(phi - psi[d])
+    float psi[3];
     int cls, k0, k1;
 };
 
@@ -48,6 +50,11 @@ __device__ __forceinline__ void brick_view(const Xdcr &x, const float O[3], cons
     v.thc = atan2f(v.rw, vz);
     float ph = atan2f(vy, vx);
     v.phc = ph < 0.f ? ph + kTwoPiF : ph;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        v.m[d] = sqrtf(x.ex[d] * x.ex[d] + x.ey[d] * x.ey[d]);
+        v.psi[d] = atan2f(x.ey[d], x.ex[d]);
+    }
     v.cls = x.cls;
 }
 
@@ -86,6 +93,70 @@ __device__ __forceinline__ bool ring_ranges(const BrickView &v, const Ring &r, f
     } else if (v.phc + delta >= kTwoPiF) {   // wraps above 2 pi: points near 0
         b0 = 0;
         b1 = min(r.nj - 1, (int)floorf((v.phc + delta - kTwoPiF) * inv));
+    }
+    return true;
+}
+
+// Azimuth index ranges of ring r (centre C) whose points can lie in the box lo <= P < hi:
+// the bounding-sphere window of ring_ranges, shrunk axis by axis to the hull of the azimuths at
+// which the ring's coordinate d = C_d + a m_d cos(phi - psi_d) lies in [lo_d, hi_d] (two arcs
+// per axis from two arccosines; their hull inside the window keeps the window one interval).
+// Margins of 1e-3 grid units and 2e-3 rad keep it conservative; candidates are then tested
+// exactly with floor(P).
+__device__ __forceinline__ bool ring_box_ranges(const BrickView &v, const Ring &r, float3 C, float rb2,
+                                                const float lo[3], const float hi[3], int &a0, int &a1, int &b0,
+                                                int &b1) {
+    a0 = 0; a1 = -1; b0 = 0; b1 = -1;
+    if (r.nj == 0) return false;
+    const float dz = v.wz0 - r.h;
+    const float dr = v.rw - r.a;
+    const float rem = rb2 - dz * dz - dr * dr;
+    if (!(rem > 0.f)) return false;
+    const float den = 4.f * r.a * v.rw;
+    float w0 = 0.f, w1 = kTwoPiF;
+    if (den > 1e-12f && rem < den) {
+        const float delta = 2.f * asinf(sqrtf(rem / den)) + 2e-3f;
+        if (delta < 3.1f) { w0 = v.phc - delta; w1 = v.phc + delta; }
+    }
+    const float Cd[3] = {C.x, C.y, C.z};
+    constexpr float kPi = 3.14159265358979f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float M = r.a * v.m[d];
+        if (M < 1e-4f) {
+            if (Cd[d] < lo[d] - M - 1e-3f || Cd[d] > hi[d] + M + 1e-3f) return false;
+            continue;
+        }
+        const float inv = 1.f / M;
+        const float cl = (lo[d] - 1e-3f - Cd[d]) * inv, ch = (hi[d] + 1e-3f - Cd[d]) * inv;
+        if (ch < -1.f || cl > 1.f) return false;
+        if (cl <= -1.f && ch >= 1.f) continue;
+        const float ah = ch >= 1.f ? 0.f : acosf(ch);
+        const float al = cl <= -1.f ? kPi : acosf(cl);
+        const float sh = kTwoPiF * floorf((w0 - v.psi[d] + kPi) * (1.f / kTwoPiF));
+        const float x0 = w0 - v.psi[d] - sh, x1 = w1 - v.psi[d] - sh;   // x0 in [-pi, pi)
+        float hl = 1e30f, hh = -1e30f;
+        const float p0[4] = {-al, ah, kTwoPiF - al, kTwoPiF + ah};
+        const float p1[4] = {-ah, al, kTwoPiF - ah, kTwoPiF + al};
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const float l = fmaxf(p0[s], x0), h = fminf(p1[s], x1);
+            if (l <= h) { hl = fminf(hl, l); hh = fmaxf(hh, h); }
+        }
+        if (hl > hh) return false;
+        w0 = hl + v.psi[d] + sh;
+        w1 = hh + v.psi[d] + sh;
+    }
+    w0 -= 2e-3f; w1 += 2e-3f;
+    if (w1 - w0 >= kTwoPiF - 1e-6f) { a1 = r.nj - 1; return true; }
+    const float sh = kTwoPiF * floorf(w0 * (1.f / kTwoPiF));
+    w0 -= sh; w1 -= sh;   // w0 in [0, 2 pi)
+    const float inv = 1.f / r.dphi;
+    a0 = max(0, (int)ceilf(w0 * inv));
+    a1 = min(r.nj - 1, (int)floorf(w1 * inv));
+    if (w1 >= kTwoPiF) {
+        b0 = 0;
+        b1 = min(r.nj - 1, (int)floorf((w1 - kTwoPiF) * inv));
     }
     return true;
 }

@@ -52,7 +52,7 @@ struct RadArgs {
     float ds2;
 };
 
-__global__ void __launch_bounds__(kRWarps * 32) k_radial_gather(RadArgs a) {
+__global__ void __launch_bounds__(kRWarps * 32, 3) k_radial_gather(RadArgs a) {
     const int4 it = a.items[blockIdx.x];
     const int cls = it.x, kb = it.y, q0 = it.z, nq = it.w;
     __shared__ float sE[kRT][9];

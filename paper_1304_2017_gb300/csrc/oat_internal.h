@@ -106,6 +106,7 @@ int launch_project(Plan &p, const float *vol, void *data, cudaStream_t s);
 int launch_backproject(Plan &p, const void *data, float *vol, cudaStream_t s);
 int count_grid_points(Plan &p, long long *out);
 int set_adjoint_attributes();
+size_t adjoint_smem_bytes();
 
 constexpr int kMaxEvents = 4096;
 
@@ -119,13 +120,15 @@ namespace oat {
 
 // (u, v) = a (cos phi_j, sin phi_j), phi_j = j * dphi in FP32.  Explicitly rounded so that
 // every kernel evaluates exactly the same values.
-__device__ __forceinline__ void ring_uv(const Ring &r, int j, float &u, float &v) {
-    float phi = __fmul_rn(__int2float_rn(j), r.dphi);
+__device__ __forceinline__ void ring_uv(float a, float dphi, int j, float &u, float &v) {
+    float phi = __fmul_rn(__int2float_rn(j), dphi);
     float s, c;
     sincosf(phi, &s, &c);
-    u = __fmul_rn(r.a, c);
-    v = __fmul_rn(r.a, s);
+    u = __fmul_rn(a, c);
+    v = __fmul_rn(a, s);
 }
+
+__device__ __forceinline__ void ring_uv(const Ring &r, int j, float &u, float &v) { ring_uv(r.a, r.dphi, j, u, v); }
 
 // Ring centre in index coordinates for one transducer: B = O + h e_z.
 __device__ __forceinline__ float3 ring_base(const float O[3], const float ez[3], float h) {

@@ -222,6 +222,7 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
         bc.smem = node_bytes * (size_t)(B + 1) * (B + 1) * (B + 1);
     };
     tile(p->adj, kBA, 2 * sizeof(int));
+    p->adj.smem = adjoint_smem_bytes();
     {
         // contributions one transducer adds to one node: 8 cells x (shells crossing a cell:
         // diameter sqrt(3) over the shell spacing, + 2) x (2 rings x 3 points, + margin)
