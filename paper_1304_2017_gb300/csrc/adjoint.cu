@@ -74,16 +74,6 @@ __device__ __forceinline__ void sadd(int *hi, unsigned int *lo, int idx, float x
     }
 }
 
-// Ring record of the flattened candidate list of one warp: ring centre, radius, azimuth step,
-// its index ranges [ja, ja + na) and [jb, ...), and the ring's first position in the list.
-struct RingSlot {
-    float cx, cy, cz, a;
-    float dphi;
-    int ja, na, jb;
-    int start;
-    int pad[3];
-};
-
 constexpr int kQueue = 64;   // per-warp queue of owned points (power of two, >= 63)
 
 // Scatter one owned point (cell-local weights wx, wy, wz; first node b) with value gq.
@@ -151,51 +141,15 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
             const int off = __ldg(a.t.ring_off + ck);
             int qh = 0, qt = 0;   // queue head and tail (warp-uniform)
             for (int ib = ilo; ib <= ihi; ib += 32) {
-                // one lane per ring: azimuth windows clipped to the brick
-                const int i = ib + lane;
-                int a0 = 0, a1 = -1, b0 = 0, b1 = -1;
-                Ring r;
-                r.h = 0.f; r.a = 0.f; r.dphi = 0.f; r.nj = 0;
-                float3 Bq = make_float3(0.f, 0.f, 0.f);
-                if (i <= ihi) {
-                    r = a.t.rings[off + i];
-                    Bq = ring_base(a.O, v.ez, r.h);
-                    ring_box_ranges(v, r, Bq, rb2, blo, bhi, a0, a1, b0, b1);
-                }
-                const int na = max(0, a1 - a0 + 1), nb = max(0, b1 - b0 + 1), n = na + nb;
-                const unsigned ne = __ballot_sync(0xffffffffu, n > 0);
-                if (ne == 0u) continue;
-                int incl = n;   // inclusive prefix over lanes
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int t = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += t;
-                }
-                const int total = __shfl_sync(0xffffffffu, incl, 31);
-                if (n > 0) {
-                    RingSlot &sl = ws[__popc(ne & lt_mask)];
-                    sl.cx = Bq.x; sl.cy = Bq.y; sl.cz = Bq.z; sl.a = r.a;
-                    sl.dphi = r.dphi; sl.ja = a0; sl.na = na; sl.jb = b0; sl.start = incl - n;
-                }
-                __syncwarp();
-                const int nre = __popc(ne);
+                int nre;
+                const int total = ring_batch(v, a.t.rings, off, ib, ihi, a.O, rb2, blo, bhi, ws, lane, &nre);
+                if (total == 0) continue;
                 const int my_start = lane < nre ? ws[lane].start : 0x7fffffff;
-                // the warp's candidates, flattened: candidate f + lane belongs to the ring slot
-                // counted by the ring starts at or before it
                 for (int f = 0; f < total; f += 32) {
-                    const int before = __popc(__ballot_sync(0xffffffffu, my_start <= f));
-                    const unsigned inside = __reduce_or_sync(
-                        0xffffffffu, (my_start > f && my_start < f + 32) ? (1u << (my_start - f)) : 0u);
-                    const int cidx = f + lane;
+                    float3 P;
                     bool own = false;
                     float4 ent;
-                    if (cidx < total) {
-                        const int si = before - 1 + __popc(inside & ((2u << lane) - 1u));
-                        const RingSlot sl = ws[si];
-                        const int o2 = cidx - sl.start;
-                        const int j = o2 < sl.na ? sl.ja + o2 : sl.jb + (o2 - sl.na);
-                        float uu, vv;
-                        ring_uv(sl.a, sl.dphi, j, uu, vv);
-                        const float3 P = ring_point(make_float3(sl.cx, sl.cy, sl.cz), v.ex, v.ey, uu, vv);
+                    if (batch_point(ws, f, lane, my_start, total, v, P)) {
                         const float fx = floorf(P.x), fy = floorf(P.y), fz = floorf(P.z);
                         const int lx = (int)fx - L[0], ly = (int)fy - L[1], lz = (int)fz - L[2];
                         own = (unsigned)lx < (unsigned)E[0] && (unsigned)ly < (unsigned)E[1] && (unsigned)lz < (unsigned)E[2];
@@ -243,16 +197,16 @@ __global__ void k_finish_t(const long long *__restrict__ vacc, float *__restrict
         vol[i] = (float)((double)vacc[i] * unit);
 }
 
-int launch_backproject(Plan &p, const void *data, float *vol, cudaStream_t s) {
+static int backproject_with(Plan &p, const void *data, float *vol, cudaStream_t s, long long *vacc, unsigned int *amax) {
     const size_t N = (size_t)p.nx * p.ny * p.nz, M = (size_t)p.Q * p.K;
-    cudaError_t e = cudaMemsetAsync(p.d_amax + 1, 0, sizeof(unsigned int), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p.d_vacc, 0, sizeof(long long) * N, s);
+    cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(unsigned int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(vacc, 0, sizeof(long long) * N, s);
     if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_backproject: memset: ") + cudaGetErrorString(e));
-    k_absmax<<<(unsigned)std::min<size_t>((M + 255) / 256, 152 * 8), 256, 0, s>>>(data, M, p.g.data_dtype, p.d_amax + 1);
+    k_absmax<<<(unsigned)std::min<size_t>((M + 255) / 256, 152 * 8), 256, 0, s>>>(data, M, p.g.data_dtype, amax);
     AdjArgs a;
     a.t = p.t; a.y = data;
-    a.vacc = (unsigned long long *)p.d_vacc;
-    a.amax = p.d_amax + 1;
+    a.vacc = (unsigned long long *)vacc;
+    a.amax = amax;
     a.nx = p.nx; a.ny = p.ny; a.nz = p.nz; a.K = p.K; a.Q = p.Q;
     for (int d = 0; d < 3; ++d) { a.nb[d] = p.adj.nb[d]; a.bs[d] = p.adj.bs[d]; a.O[d] = p.O[d]; }
     a.qchunk = p.adj.qchunk; a.kspan = p.adj.kspan; a.qpass = p.adj_qpass;
@@ -271,10 +225,14 @@ int launch_backproject(Plan &p, const void *data, float *vol, cudaStream_t s) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_backproject: k_brick_gather_t: ") + cudaGetErrorString(e));
     k_finish_t<<<(unsigned)std::min<size_t>((N + 255) / 256, 152 * 16), 256, 0, s>>>(
-        (const long long *)p.d_vacc, vol, N, p.d_amax + 1, p.gscale, p.g.spacing_mm * p.g.spacing_mm);
+        (const long long *)vacc, vol, N, amax, p.gscale, p.g.spacing_mm * p.g.spacing_mm);
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_backproject: k_finish_t: ") + cudaGetErrorString(e));
     return OAT_OK;
+}
+
+int launch_backproject(Plan &p, const void *data, float *vol, cudaStream_t s) {
+    return backproject_with(p, data, vol, s, p.d_vacc, p.d_amax + 1);
 }
 
 size_t adjoint_smem_bytes() {

@@ -161,6 +161,69 @@ __device__ __forceinline__ bool ring_box_ranges(const BrickView &v, const Ring &
     return true;
 }
 
+// Ring record of a warp's flattened candidate list: ring centre, radius, azimuth step, its
+// index ranges [ja, ja + na) and [jb, ...), and the ring's first position in the list.
+struct RingSlot {
+    float cx, cy, cz, a;
+    float dphi;
+    int ja, na, jb;
+    int start;
+    int pad[3];
+};
+
+// One lane per ring i = ib + lane (i <= ihi) of shell ck: the ring's azimuth windows clipped to the
+// brick, written compacted (non-empty rings only, in ring order) to the warp's slots ws.  Returns
+// the number of candidates of the batch; *nre = number of filled slots.  Warp-collective.
+__device__ __forceinline__ int ring_batch(const BrickView &v, const Ring *__restrict__ rings, int off, int ib, int ihi,
+                                          const float O[3], float rb2, const float blo[3], const float bhi[3],
+                                          RingSlot *ws, int lane, int *nre) {
+    const int i = ib + lane;
+    int a0 = 0, a1 = -1, b0 = 0, b1 = -1;
+    Ring r;
+    r.h = 0.f; r.a = 0.f; r.dphi = 0.f; r.nj = 0;
+    float3 Bq = make_float3(0.f, 0.f, 0.f);
+    if (i <= ihi) {
+        r = rings[off + i];
+        Bq = ring_base(O, v.ez, r.h);
+        ring_box_ranges(v, r, Bq, rb2, blo, bhi, a0, a1, b0, b1);
+    }
+    const int na = max(0, a1 - a0 + 1), nb = max(0, b1 - b0 + 1), n = na + nb;
+    const unsigned ne = __ballot_sync(0xffffffffu, n > 0);
+    *nre = __popc(ne);
+    if (ne == 0u) return 0;
+    int incl = n;   // inclusive prefix over lanes
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (n > 0) {
+        RingSlot &sl = ws[__popc(ne & ((1u << lane) - 1u))];
+        sl.cx = Bq.x; sl.cy = Bq.y; sl.cz = Bq.z; sl.a = r.a;
+        sl.dphi = r.dphi; sl.ja = a0; sl.na = na; sl.jb = b0; sl.start = incl - n;
+    }
+    __syncwarp();
+    return __shfl_sync(0xffffffffu, incl, 31);
+}
+
+// Candidate f + lane of a ring batch (my_start: start of slot `lane`, or INT_MAX): its lattice
+// point, through the same functions in both directions.  Warp-collective; returns false for
+// lanes past the end of the list.
+__device__ __forceinline__ bool batch_point(const RingSlot *ws, int f, int lane, int my_start, int total,
+                                            const BrickView &v, float3 &P) {
+    const int before = __popc(__ballot_sync(0xffffffffu, my_start <= f));
+    const unsigned inside =
+        __reduce_or_sync(0xffffffffu, (my_start > f && my_start < f + 32) ? (1u << (my_start - f)) : 0u);
+    const int cidx = f + lane;
+    if (cidx >= total) return false;
+    const RingSlot sl = ws[before - 1 + __popc(inside & ((2u << lane) - 1u))];
+    const int o2 = cidx - sl.start;
+    const int j = o2 < sl.na ? sl.ja + o2 : sl.jb + (o2 - sl.na);
+    float uu, vv;
+    ring_uv(sl.a, sl.dphi, j, uu, vv);
+    P = ring_point(make_float3(sl.cx, sl.cy, sl.cz), v.ex, v.ey, uu, vv);
+    return true;
+}
+
 // Lowest cell L and cell counts E (<= bs) of brick id in a grid of nb[3] bricks (x fastest)
 // tiling the cells [-1, n-1] of each axis.
 __device__ __forceinline__ void brick_box(int id, const int nb[3], const int bs[3], const int n[3], int L[3], int E[3]) {

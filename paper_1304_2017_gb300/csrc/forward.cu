@@ -11,6 +11,7 @@
 #include <cuda_fp16.h>
 
 #include "brick.cuh"
+#include <cstdlib>
 
 namespace oat {
 
@@ -202,7 +203,178 @@ static int launch_project_radial(Plan &p, const float *vol, void *data, cudaStre
     return OAT_OK;
 }
 
-int launch_project(Plan &p, const float *vol, void *data, cudaStream_t s) { return launch_project_radial(p, vol, data, s); }
+static int launch_project_brick(Plan &p, const float *vol, void *data, cudaStream_t s);
+
+int launch_project(Plan &p, const float *vol, void *data, cudaStream_t s) {
+    return p.fwd_radial ? launch_project_radial(p, vol, data, s) : launch_project_brick(p, vol, data, s);
+}
+
+// ---------------------------------------------------------------------------- bricks
+// k_brick_gather: one block per work item (brick of kBF^3 cells, range of transducers).  The
+// brick's (kBF+1)^3 nodes are staged in shared memory (zero outside the grid).  A warp takes one
+// (transducer, shell) unit at a time; one lane per ring computes the ring's azimuth window
+// clipped to the brick, the candidates are spread evenly over the lanes (brick.cuh), and each
+// point whose cell floor(P) lies in the brick is interpolated from shared memory.  The unit's
+// compensated FP32 sum is added to g[q][k] as a 64-bit fixed-point integer (one atomic per unit),
+// so the total does not depend on the order in which bricks finish.
+constexpr int kFwdThreads = 1024;
+
+struct FwdArgs {
+    DevTables t;
+    const float *vol;
+    unsigned long long *gacc;     // [Q][K] fixed-point sums
+    const unsigned int *amax;     // bits of max |alpha|
+    int nx, ny, nz, K, Q;
+    int nb[3], bs[3];
+    int qchunk, kspan;
+    float O[3];
+    float R0, dR;
+    double bound_pts;             // max lattice points of one shell
+};
+
+template <int B>
+__global__ void __launch_bounds__(kFwdThreads, 1) k_brick_gather(FwdArgs a) {
+    extern __shared__ float sv[];   // (B+1)^3 nodes of the brick, then the warps' ring slots
+    constexpr int S1 = B + 1, S2 = (B + 1) * (B + 1), NN = (B + 1) * (B + 1) * (B + 1);
+    constexpr int NNp = NN + ((NN & 3) ? 4 - (NN & 3) : 0);
+    RingSlot *slots = (RingSlot *)(sv + NNp);
+    const int nqc = (a.Q + a.qchunk - 1) / a.qchunk;
+    const int brick = blockIdx.x / nqc;
+    const int q0 = (blockIdx.x % nqc) * a.qchunk;
+    const int q1 = min(a.Q, q0 + a.qchunk);
+    int L[3], E[3];
+    {
+        const int n[3] = {a.nx, a.ny, a.nz};
+        brick_box(brick, a.nb, a.bs, n, L, E);
+    }
+    for (int idx = threadIdx.x; idx < NN; idx += blockDim.x) {
+        const int x = idx % S1 + L[0], y = (idx / S1) % S1 + L[1], z = idx / S2 + L[2];
+        float val = 0.f;
+        if (x >= 0 && x < a.nx && y >= 0 && y < a.ny && z >= 0 && z < a.nz) val = __ldg(a.vol + ((size_t)z * a.ny + y) * a.nx + x);
+        sv[idx] = val;
+    }
+    __syncthreads();
+
+    const float c[3] = {L[0] + 0.5f * E[0], L[1] + 0.5f * E[1], L[2] + 0.5f * E[2]};
+    const float blo[3] = {(float)L[0], (float)L[1], (float)L[2]};
+    const float bhi[3] = {(float)(L[0] + E[0]), (float)(L[1] + E[1]), (float)(L[2] + E[2])};
+    const float rb = 0.5f * sqrtf((float)(E[0] * E[0] + E[1] * E[1] + E[2] * E[2])) + 0.05f;
+    const float rb2 = rb * rb;
+    const double scale = pow2_scale(a.bound_pts * (double)__uint_as_float(*a.amax), 61);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    RingSlot *ws = slots + warp * 32;
+    const int units = (q1 - q0) * a.kspan;
+    int vq = -1;
+    BrickView v;
+
+    for (int u = warp; u < units; u += nwarps) {
+        const int q = q0 + u / a.kspan;
+        if (q != vq) { brick_view(a.t.xd[q], a.O, c, rb, a.R0, a.dR, a.K, v); vq = q; }
+        const int k = v.k0 + u % a.kspan;
+        if (k > v.k1) continue;
+        const int ck = v.cls * a.K + k;
+        const int nr = __ldg(a.t.ring_cnt + ck);
+        int ilo, ihi;
+        if (!shell_ring_range(v, __ldg(a.t.Rk + k), nr, rb2, ilo, ihi)) continue;
+        const int off = __ldg(a.t.ring_off + ck);
+        float acc = 0.f, err = 0.f;
+        for (int ib = ilo; ib <= ihi; ib += 32) {
+            int nre;
+            const int total = ring_batch(v, a.t.rings, off, ib, ihi, a.O, rb2, blo, bhi, ws, lane, &nre);
+            if (total == 0) continue;
+            const int my_start = lane < nre ? ws[lane].start : 0x7fffffff;
+            for (int f = 0; f < total; f += 32) {
+                float3 P;
+                if (!batch_point(ws, f, lane, my_start, total, v, P)) continue;
+                const float fx = floorf(P.x), fy = floorf(P.y), fz = floorf(P.z);
+                const int lx = (int)fx - L[0], ly = (int)fy - L[1], lz = (int)fz - L[2];
+                if ((unsigned)lx < (unsigned)E[0] && (unsigned)ly < (unsigned)E[1] && (unsigned)lz < (unsigned)E[2]) {
+                    const float wx = P.x - fx, wy = P.y - fy, wz = P.z - fz;
+                    const float *sp = sv + lz * S2 + ly * S1 + lx;
+                    const float c00 = lerp1(sp[0], sp[1], wx), c01 = lerp1(sp[S1], sp[S1 + 1], wx);
+                    const float c10 = lerp1(sp[S2], sp[S2 + 1], wx), c11 = lerp1(sp[S2 + S1], sp[S2 + S1 + 1], wx);
+                    kadd(acc, err, lerp1(lerp1(c00, c01, wy), lerp1(c10, c11, wy), wz));
+                }
+            }
+            __syncwarp();
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float s2 = __shfl_xor_sync(0xffffffffu, acc, o);
+            const float e2 = __shfl_xor_sync(0xffffffffu, err, o);
+            kadd(acc, err, s2);
+            err += e2;
+        }
+        if (lane == 0) {
+            const long long fxp = __double2ll_rn(((double)acc + (double)err) * scale);
+            if (fxp != 0) atomicAdd(a.gacc + (size_t)q * a.K + k, (unsigned long long)fxp);
+        }
+    }
+}
+
+// D in double on the exact fixed-point sums of G; one rounding to the storage type.
+template <int DT, bool APPLY_D>
+__global__ void k_apply_d_fix(const long long *__restrict__ gacc, const double *__restrict__ wD, void *out, int Q, int K,
+                              const unsigned int *amax, double bound_pts, double ds2) {
+    const double unit = ds2 / pow2_scale(bound_pts * (double)__uint_as_float(*amax), 61);
+    const size_t n = (size_t)Q * K;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(idx % K);
+        double val;
+        if (!APPLY_D) val = (double)gacc[idx] * unit;
+        else if (k < 1 || k > K - 2) val = 0.0;
+        else val = wD[k + 1] * ((double)gacc[idx + 1] * unit) - wD[k - 1] * ((double)gacc[idx - 1] * unit);
+        store_data<DT>(out, idx, (float)val);
+    }
+}
+
+size_t forward_smem_bytes() {
+    const size_t nn = (size_t)(kBF + 1) * (kBF + 1) * (kBF + 1);
+    return sizeof(float) * (nn + ((nn & 3) ? 4 - (nn & 3) : 0)) + sizeof(RingSlot) * kFwdThreads;
+}
+
+int set_forward_attributes() {
+    cudaError_t e = cudaFuncSetAttribute(k_brick_gather<kBF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)forward_smem_bytes());
+    return e == cudaSuccess ? OAT_OK : set_error(OAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+}
+
+static int launch_project_brick(Plan &p, const float *vol, void *data, cudaStream_t s) {
+    const size_t N = (size_t)p.nx * p.ny * p.nz;
+    cudaError_t e = cudaMemsetAsync(p.d_amax, 0, sizeof(unsigned int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.d_gacc, 0, sizeof(long long) * (size_t)p.Q * p.K, s);
+    if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_project: memset: ") + cudaGetErrorString(e));
+    k_absmax<<<(unsigned)std::min<size_t>((N + 255) / 256, 152 * 8), 256, 0, s>>>(vol, N, OAT_F32, p.d_amax);
+    FwdArgs a;
+    a.t = p.t; a.vol = vol;
+    a.gacc = (unsigned long long *)p.d_gacc;
+    a.amax = p.d_amax;
+    a.nx = p.nx; a.ny = p.ny; a.nz = p.nz; a.K = p.K; a.Q = p.Q;
+    for (int d = 0; d < 3; ++d) { a.nb[d] = p.fwd.nb[d]; a.bs[d] = p.fwd.bs[d]; a.O[d] = p.O[d]; }
+    a.qchunk = p.fwd.qchunk; a.kspan = p.fwd.kspan;
+    a.R0 = p.R0; a.dR = p.dR;
+    a.bound_pts = (double)p.max_shell_points;
+    const bool prof = p.profiling && p.ev_used[0] + 2 <= (int)p.ev[0].size();
+    if (prof) cudaEventRecord(p.ev[0][p.ev_used[0]], s);
+    k_brick_gather<kBF><<<(unsigned)p.fwd.items, kFwdThreads, p.fwd.smem, s>>>(a);
+    if (prof) { cudaEventRecord(p.ev[0][p.ev_used[0] + 1], s); p.ev_used[0] += 2; }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_project: k_brick_gather: ") + cudaGetErrorString(e));
+    const size_t n = (size_t)p.Q * p.K;
+    const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
+    const int dt = p.g.data_dtype;
+    const double bp = (double)p.max_shell_points, ds2 = p.g.spacing_mm * p.g.spacing_mm;
+    const long long *g = (const long long *)p.d_gacc;
+#define OAT_APPLY(DTV, AD) k_apply_d_fix<DTV, AD><<<blocks, 256, 0, s>>>(g, p.t.wD64, data, p.Q, p.K, p.d_amax, bp, ds2)
+    if (p.g.apply_d) {
+        if (dt == OAT_F32) OAT_APPLY(OAT_F32, true); else if (dt == OAT_F16) OAT_APPLY(OAT_F16, true); else OAT_APPLY(OAT_BF16, true);
+    } else {
+        if (dt == OAT_F32) OAT_APPLY(OAT_F32, false); else if (dt == OAT_F16) OAT_APPLY(OAT_F16, false); else OAT_APPLY(OAT_BF16, false);
+    }
+#undef OAT_APPLY
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_project: k_apply_d: ") + cudaGetErrorString(e));
+    return OAT_OK;
+}
 
 // ---------------------------------------------------------------------------- point counting
 

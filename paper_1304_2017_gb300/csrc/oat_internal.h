@@ -60,6 +60,7 @@ struct BrickCfg {
     size_t smem = 0;
 };
 
+constexpr int kBF = 32;     // projector brick edge: (kBF+1)^3 float nodes in shared memory
 constexpr int kBA = 24;     // backprojector brick edge: (kBA+1)^3 pairs of 32-bit node-sum halves in shared memory
 
 struct Plan {
@@ -76,7 +77,8 @@ struct Plan {
     long long max_shell_points = 0;   // largest N_i-ring lattice of one shell (fixed-point bound)
     float gscale = 1.f;               // max |g'| / max |y|: 2 max_k C_D/tau_k with D, 1 without
     int adj_qpass = 1;                // transducers per backprojector pass (bounds the 32-bit halves)
-    BrickCfg adj;                      // backprojector brick tiling
+    BrickCfg fwd, adj;                 // brick tilings of the projector and the backprojector
+    bool fwd_radial = false;           // projector kernel: radial lanes or bricks
     const int4 *d_ritems = nullptr;    // radial work items (class, first shell, first in qlist, count)
     long long n_ritems = 0;
     long long table_bytes = 0, scratch_bytes = 0;
@@ -106,6 +108,8 @@ int launch_project(Plan &p, const float *vol, void *data, cudaStream_t s);
 int launch_backproject(Plan &p, const void *data, float *vol, cudaStream_t s);
 int count_grid_points(Plan &p, long long *out);
 int set_adjoint_attributes();
+int set_forward_attributes();
+size_t forward_smem_bytes();
 size_t adjoint_smem_bytes();
 
 constexpr int kMaxEvents = 4096;

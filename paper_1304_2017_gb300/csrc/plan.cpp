@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <cstdlib>
 #include <new>
 
 #include "oat_internal.h"
@@ -221,6 +222,8 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
         bc.items = bricks * ((Q + bc.qchunk - 1) / bc.qchunk);
         bc.smem = node_bytes * (size_t)(B + 1) * (B + 1) * (B + 1);
     };
+    tile(p->fwd, kBF, sizeof(float));
+    p->fwd.smem = forward_smem_bytes();
     tile(p->adj, kBA, 2 * sizeof(int));
     p->adj.smem = adjoint_smem_bytes();
     {
@@ -309,7 +312,11 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
     if ((e = cudaMalloc(&p->d_amax, 256)) != cudaSuccess) return fail(e, "cudaMalloc(scale scratch)");
     p->d_count = (unsigned long long *)((char *)p->d_amax + 128);
     p->scratch_bytes = (long long)(g_bytes + v_bytes + 256);
-    if (set_adjoint_attributes() != OAT_OK) {
+    {
+        const char *env = std::getenv("OAT_FWD");
+        p->fwd_radial = !(env && std::string(env) == "brick");
+    }
+    if (set_forward_attributes() != OAT_OK || set_adjoint_attributes() != OAT_OK) {
         std::string msg = std::string("oat_plan_create: ") + oat_last_error();
         fail(cudaSuccess, "kernel attributes");
         return set_error(OAT_ERR_CUDA, msg);

@@ -61,7 +61,8 @@ def _load():
                                          ctypes.POINTER(ctypes.c_longlong)]
     lib.oat_last_error.restype = ctypes.c_char_p
     lib.oat_version.restype = ctypes.c_int
-    for name in ("oat_plan_create", "oat_plan_destroy", "oat_project", "oat_backproject", "oat_plan_query",
+    for name in ("oat_plan_create", "oat_plan_destroy", "oat_project", "oat_backproject",
+                 "oat_plan_query",
                  "oat_plan_set_profiling", "oat_plan_kernel_time"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
