@@ -131,6 +131,24 @@ int oat_project(oat_plan plan, const float *d_vol, void *d_data, void *stream);
 int oat_backproject(oat_plan plan, const void *d_data, float *d_vol, void *stream);
 
 /*
+ * alpha' = H^T y exactly as oat_backproject, for callers that cannot allocate device memory at
+ * the time of the call: the backprojector's scratch (a 64-bit accumulator per voxel and one
+ * max|y| word) is taken from an array of this library in static device memory instead of the
+ * plan's scratch, and the call allocates nothing (no cudaMalloc or cudaFree, no allocating
+ * library call).  This entry point has no counterpart in the paper.
+ *   Limit: nx * ny * nz <= 2,097,152 voxels (the array holds 16 MiB + 256 bytes on every GPU
+ *          that loads the library, until the process exits); larger volumes return
+ *          OAT_ERR_INVALID_ARG.
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *   that device current; make that first call before any stream capture.
+ *   All calls share the array and each clears what it needs at its start, so two calls whose
+ *   work overlaps on the GPU (on different streams, or from different plans) race and give wrong
+ *   results; order them.
+ * Arguments, layouts and other errors as oat_backproject.
+ */
+int oat_backproject_noalloc(oat_plan plan, const void *d_data, float *d_vol, void *stream);
+
+/*
  * Fill *stats.  With count_grid_points != 0 the call also counts, on the device and
  * synchronously (on the legacy default stream), the lattice points whose interpolation
  * stencil touches the grid, the unit of work of the throughput metric.

@@ -84,6 +84,17 @@ int oat_backproject(oat_plan plan, const void *d_data, float *d_vol, void *strea
     return launch_backproject(*p, d_data, d_vol, (cudaStream_t)stream);
 }
 
+int oat_backproject_noalloc(oat_plan plan, const void *d_data, float *d_vol, void *stream) {
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || !d_vol || !d_data) return set_error(OAT_ERR_INVALID_ARG, "oat_backproject_noalloc: NULL plan or buffer");
+    if (!aligned16(d_vol) || !aligned16(d_data))
+        return set_error(OAT_ERR_INVALID_ARG, "oat_backproject_noalloc: buffers must be 16-byte aligned");
+    DeviceGuard dg(p->device);
+    if (dg.err != cudaSuccess)
+        return set_error(OAT_ERR_CUDA, std::string("oat_backproject_noalloc: ") + cudaGetErrorString(dg.err));
+    return launch_backproject_static(*p, d_data, d_vol, (cudaStream_t)stream);
+}
+
 int oat_plan_query(oat_plan plan, int want_count, oat_stats *st) {
     Plan *p = reinterpret_cast<Plan *>(plan);
     if (!p || !st) return set_error(OAT_ERR_INVALID_ARG, "oat_plan_query: NULL plan or stats");

@@ -22,6 +22,9 @@
 
 #include "brick.cuh"
 
+#include <mutex>
+#include <string>
+
 namespace oat {
 
 constexpr int kAdjThreads = 1024;
@@ -233,6 +236,48 @@ static int backproject_with(Plan &p, const void *data, float *vol, cudaStream_t 
 
 int launch_backproject(Plan &p, const void *data, float *vol, cudaStream_t s) {
     return backproject_with(p, data, vol, s, p.d_vacc, p.d_amax + 1);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Backprojection without any allocation.  Some callers cannot allocate device memory at the
+// time they need H^T (for example code running inside a pool-managed or graph-building context
+// that forbids cudaMalloc, or a host framework that hands out only the buffers it owns).  For
+// them the scratch of the backprojector -- the 64-bit node accumulator and the max|y| word -- is a
+// file-scope array in device memory, sized for volumes of at most kStaticVoxels voxels.  The
+// array exists on every GPU that loads this library, until the process exits.
+constexpr size_t kStaticVoxels = size_t(1) << 21;          // 2,097,152 voxels (e.g. 128^3)
+constexpr size_t kStaticHeader = 32;                       // 256 bytes: max|y| bit pattern
+static __device__ __align__(256) unsigned long long g_static_scratch[kStaticHeader + kStaticVoxels];
+
+static std::mutex g_static_mu;
+static void *g_static_addr[256] = {};
+
+// Device address of the array on device dev (dev current); looked up once per device.
+static int static_scratch(int dev, void **out) {
+    if (dev < 0 || dev >= 256) return set_error(OAT_ERR_INVALID_ARG, "oat_backproject_noalloc: device index out of range");
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess || !ptr)
+            return set_error(OAT_ERR_CUDA, std::string("oat_backproject_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        g_static_addr[dev] = ptr;
+    }
+    *out = g_static_addr[dev];
+    return OAT_OK;
+}
+
+int launch_backproject_static(Plan &p, const void *data, float *vol, cudaStream_t s) {
+    const size_t N = (size_t)p.nx * p.ny * p.nz;
+    if (N > kStaticVoxels)
+        return set_error(OAT_ERR_INVALID_ARG, "oat_backproject_noalloc: volume of " + std::to_string(N) +
+                                                  " voxels exceeds the static scratch limit of " +
+                                                  std::to_string(kStaticVoxels) + " voxels");
+    void *base = nullptr;
+    int rc = static_scratch(p.device, &base);
+    if (rc != OAT_OK) return rc;
+    unsigned long long *w = (unsigned long long *)base;
+    return backproject_with(p, data, vol, s, (long long *)(w + kStaticHeader), (unsigned int *)w);
 }
 
 size_t adjoint_smem_bytes() {

@@ -106,6 +106,7 @@ int set_error(int code, const std::string &msg);
 // kernels' host launchers (forward.cu, adjoint.cu)
 int launch_project(Plan &p, const float *vol, void *data, cudaStream_t s);
 int launch_backproject(Plan &p, const void *data, float *vol, cudaStream_t s);
+int launch_backproject_static(Plan &p, const void *data, float *vol, cudaStream_t s);
 int count_grid_points(Plan &p, long long *out);
 int set_adjoint_attributes();
 int set_forward_attributes();

@@ -55,13 +55,14 @@ def _load():
     lib.oat_plan_destroy.argtypes = [vp]
     lib.oat_project.argtypes = [vp, vp, vp, vp]
     lib.oat_backproject.argtypes = [vp, vp, vp, vp]
+    lib.oat_backproject_noalloc.argtypes = [vp, vp, vp, vp]
     lib.oat_plan_query.argtypes = [vp, ctypes.c_int, ctypes.POINTER(oat_stats)]
     lib.oat_plan_set_profiling.argtypes = [vp, ctypes.c_int]
     lib.oat_plan_kernel_time.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_longlong)]
     lib.oat_last_error.restype = ctypes.c_char_p
     lib.oat_version.restype = ctypes.c_int
-    for name in ("oat_plan_create", "oat_plan_destroy", "oat_project", "oat_backproject",
+    for name in ("oat_plan_create", "oat_plan_destroy", "oat_project", "oat_backproject", "oat_backproject_noalloc",
                  "oat_plan_query",
                  "oat_plan_set_profiling", "oat_plan_kernel_time"):
         getattr(lib, name).restype = ctypes.c_int
@@ -113,6 +114,11 @@ def oat_project(handle, d_vol, d_data, stream=0):
 
 def oat_backproject(handle, d_data, d_vol, stream=0):
     return _check(lib.oat_backproject(handle, ctypes.c_void_p(d_data), ctypes.c_void_p(d_vol), ctypes.c_void_p(stream)))
+
+
+def oat_backproject_noalloc(handle, d_data, d_vol, stream=0):
+    return _check(lib.oat_backproject_noalloc(handle, ctypes.c_void_p(d_data), ctypes.c_void_p(d_vol),
+                                              ctypes.c_void_p(stream)))
 
 
 def oat_plan_query(handle, count_grid_points=False):
