@@ -29,7 +29,7 @@ sys.path.insert(0, ROOT)
 METRIC = "H+H^T G interp-samples/s and % HBM/L2 roofline; PLS-TV time to 1e-3 residual"
 UNIT = "interp-samples/s"
 WORKLOAD = "256^3 @ 0.2 mm, 200 ellipsoids, 128 rings x 180 views (23040 transducers) on 65 mm, K=1536 @ 20 MHz, c=1.5"
-# FP32 operations charged to one interpolated sample ("Roofline"): lattice point
+# FP32 operations charged to one interpolated sample: lattice point
 # 6 FMA (12), floor 3, fraction 3, 7 lerps (7 sub + 7 FMA = 21), accumulate 1.
 FLOP_PER_SAMPLE = 40.0
 N_SM = 152
