@@ -162,6 +162,27 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_capture():
+    """The workload restricted to 64 transducers (rings 10, 30, 50, 64, 70, 90, 110, 120 x views
+    0, 20, ..., 140): 2.9e9 interpolations per operator, ~2 GB on the device."""
+    import torch
+
+    from paper_1304_2017_gb300 import oat
+    from paper_1304_2017_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    g = W.config("c2")
+    qs = [r * 180 + v for r in (10, 30, 50, 64, 70, 90, 110, 120) for v in range(0, 160, 20)]
+    sub = g.subset(qs)
+    plan = oat.Plan(sub)
+    alpha = torch.from_numpy(W.phantom("c2", g)).cuda()
+    y = torch.from_numpy(W.random_data(sub)).cuda()
+    for _ in range(2):
+        plan.project(alpha)
+        plan.backproject(y)
+    torch.cuda.synchronize()
+    plan.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -171,9 +192,13 @@ def main():
     ap.add_argument("--config", default="c2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--capture", action="store_true",
+                    help="small case for ncu captures: the 256^3 workload on 64 transducers, H and H^T twice")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.capture:
+        return run_capture()
 
     import torch
     import torch.distributed as dist
