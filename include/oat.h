@@ -122,8 +122,9 @@ int oat_project(oat_plan plan, const float *d_vol, void *d_data, void *stream);
 /*
  * alpha' = H^T y (or G^T y when apply_d = 0)  -- the adjoints of Sec. II.B.  Exact transpose
  * of oat_project: the same FP32 lattice points, the same interpolation weights; D^T is the
- * exact transpose of D including its zero boundary rows.  Computed as a gather per voxel with
- * no floating-point atomics.
+ * exact transpose of D including its zero boundary rows.  Computed brick by brick: each brick of
+ * voxels sums the weighted lattice points that fall in its cells as exact fixed-point integers,
+ * so there are no floating-point atomics and the result does not depend on execution order.
  *   d_data  device, [Q][K] of data_dtype, read only
  *   d_vol   device, float32 [nz][ny][nx], fully overwritten
  * Errors: as oat_project.

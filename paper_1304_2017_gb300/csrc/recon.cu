@@ -35,9 +35,10 @@ __global__ void __launch_bounds__(kRThreads) k_fista_residual(long long n, const
                                                               float beta, float *r, double *acc) {
     double s0 = 0.0, s1 = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const float h = hx[i], uu = u[i], d = h - uu;
+        const float h = hx[i], uu = u[i];
         const float prev = hp[i];
-        s0 += (double)d * d;
+        const double d = (double)h - (double)uu;
+        s0 += d * d;
         s1 += (double)uu * uu;
         r[i] = fmaf(beta, h - prev, h) - uu;
     }

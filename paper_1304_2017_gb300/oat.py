@@ -60,6 +60,14 @@ def _load():
     lib.oat_plan_set_profiling.argtypes = [vp, ctypes.c_int]
     lib.oat_plan_kernel_time.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_longlong)]
+    ll, f32, i32 = ctypes.c_longlong, ctypes.c_float, ctypes.c_int
+    lib.oat_fista_residual.argtypes = [ll, vp, vp, vp, f32, vp, vp, vp]
+    lib.oat_tv_prox.argtypes = [i32, i32, i32, vp, vp, f32, f32, i32, vp, vp, vp]
+    lib.oat_fista_momentum.argtypes = [ll, vp, vp, f32, vp, vp]
+    lib.oat_dot.argtypes = [ll, vp, vp, vp, vp]
+    lib.oat_tv_value.argtypes = [i32, i32, i32, vp, vp, vp]
+    for name in ("oat_fista_residual", "oat_tv_prox", "oat_fista_momentum", "oat_dot", "oat_tv_value"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.oat_last_error.restype = ctypes.c_char_p
     lib.oat_version.restype = ctypes.c_int
     for name in ("oat_plan_create", "oat_plan_destroy", "oat_project", "oat_backproject", "oat_backproject_noalloc",
@@ -135,6 +143,33 @@ def oat_plan_kernel_time(handle, which, reset=False):
     ms, n = ctypes.c_double(), ctypes.c_longlong()
     _check(lib.oat_plan_kernel_time(handle, int(which), int(bool(reset)), ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+# ---- reconstruction kernels (include/oat_recon.h) ------------------------------------------
+
+def _p(x):
+    return ctypes.c_void_p(x)
+
+
+def oat_fista_residual(n, hx, hx_prev, u, beta, r, acc, stream=0):
+    return _check(lib.oat_fista_residual(n, _p(hx), _p(hx_prev), _p(u), beta, _p(r), _p(acc), _p(stream)))
+
+
+def oat_tv_prox(nx, ny, nz, z, g, step, lam, iters, out, work, stream=0):
+    return _check(lib.oat_tv_prox(nx, ny, nz, _p(z), _p(g) if g else None, step, lam, iters, _p(out), _p(work),
+                                  _p(stream)))
+
+
+def oat_fista_momentum(n, a, a_prev, beta, y, stream=0):
+    return _check(lib.oat_fista_momentum(n, _p(a), _p(a_prev), beta, _p(y), _p(stream)))
+
+
+def oat_dot(n, x, y, acc, stream=0):
+    return _check(lib.oat_dot(n, _p(x), _p(y), _p(acc), _p(stream)))
+
+
+def oat_tv_value(nx, ny, nz, x, acc, stream=0):
+    return _check(lib.oat_tv_value(nx, ny, nz, _p(x), _p(acc), _p(stream)))
 
 
 # ---- torch wrapper ---------------------------------------------------------------------
