@@ -162,6 +162,18 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_learned(args):
+    """PLS-TV time to a 1e-3 relative data residual from zero and from the learned warm start."""
+    from paper_1304_2017_gb300 import warmstart
+    kw = {}
+    for item in filter(None, args.learned_args.split(",")):
+        k, v = item.split("=")
+        kw[k] = float(v) if "." in v or "e" in v else int(v)
+    out = warmstart.run(**kw)
+    out["metric"] = "PLS-TV GPU seconds to a 1e-3 relative data residual (zero start vs learned warm start)"
+    print(json.dumps(out), flush=True)
+
+
 def run_capture():
     """The workload restricted to 64 transducers (rings 10, 30, 50, 64, 70, 90, 110, 120 x views
     0, 20, ..., 140): 2.9e9 interpolations per operator, ~2 GB on the device."""
@@ -192,6 +204,9 @@ def main():
     ap.add_argument("--config", default="c2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--learned", action="store_true",
+                    help="learned warm start: train the U-Net on PLS-TV targets, compare time to a 1e-3 residual")
+    ap.add_argument("--learned-args", default="", help="k=v,... overrides for warmstart.run (e.g. n_train=8)")
     ap.add_argument("--capture", action="store_true",
                     help="small case for ncu captures: the 256^3 workload on 64 transducers, H and H^T twice")
     args = ap.parse_args()
@@ -199,6 +214,8 @@ def main():
         return run_reference(args)
     if args.capture:
         return run_capture()
+    if args.learned:
+        return run_learned(args)
 
     import torch
     import torch.distributed as dist

@@ -1,0 +1,408 @@
+// Kernels of the learned warm start: a small 3-D U-Net on BF16 activations (include/oat_unet.h).
+//
+// Activations are BF16, channels last: x[z][y][x][c].  Convolution weights are BF16
+// w[tap][cout][cin], tap = (dz * 3 + dy) * 3 + dx for offsets (dz - 1, dy - 1, dx - 1), zero
+// padding ('same').
+//
+// k_conv3d: implicit GEMM on the tensor cores.  Rows are 16 consecutive voxels along x (one
+// warp), columns the output channels, the reduction runs over 27 taps x input channels in
+// steps of 16; each step is one mma.sync.m16n8k16 (BF16 inputs, FP32 accumulation) per 8
+// output channels.  Epilogue: + bias, optional ReLU, BF16 store.  The input gradient of a
+// 'same' 3x3x3 convolution is the same convolution of the output gradient with the kernel
+// flipped in space and transposed in channels, so the same kernel serves the backward pass
+// (k_flip_weights builds that kernel).
+// k_conv3d_wgrad: weight and bias gradients on the FP32 cores (training only).
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <string>
+
+#include "../../include/oat_unet.h"
+#include "oat_internal.h"
+
+namespace oat {
+
+typedef __nv_bfloat16 bf16;
+
+__device__ __forceinline__ unsigned ld_pair(const bf16 *p) { return *reinterpret_cast<const unsigned *>(p); }
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                         unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+template <int COUT>
+__global__ void __launch_bounds__(128) k_conv3d(int nx, int ny, int nz, int cin, const bf16 *__restrict__ x,
+                                                const bf16 *__restrict__ w, const float *__restrict__ bias, int relu,
+                                                bf16 *__restrict__ y) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x0 = blockIdx.x * 64 + warp * 16, yy = blockIdx.y, zz = blockIdx.z;
+    const int g = lane >> 2, kq = (lane & 3) * 2;
+    float acc[COUT / 8][4];
+#pragma unroll
+    for (int n = 0; n < COUT / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+    if (x0 < nx) {
+        for (int tap = 0; tap < 27; ++tap) {
+            const int zs = zz + tap / 9 - 1, ys = yy + (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+            if (zs < 0 || zs >= nz || ys < 0 || ys >= ny) continue;
+            const int xa = x0 + g + dx, xb = xa + 8;
+            const bool oa = xa >= 0 && xa < nx, ob = xb >= 0 && xb < nx;
+            const size_t row = ((size_t)zs * ny + ys) * nx;
+            const bf16 *pa = x + (row + (oa ? xa : 0)) * cin + kq;
+            const bf16 *pb = x + (row + (ob ? xb : 0)) * cin + kq;
+            const bf16 *wt = w + ((size_t)tap * COUT + g) * cin + kq;
+            for (int c = 0; c < cin; c += 16) {
+                const unsigned a0 = oa ? ld_pair(pa + c) : 0u, a1 = ob ? ld_pair(pb + c) : 0u;
+                const unsigned a2 = oa ? ld_pair(pa + c + 8) : 0u, a3 = ob ? ld_pair(pb + c + 8) : 0u;
+#pragma unroll
+                for (int n = 0; n < COUT / 8; ++n) {
+                    const bf16 *wp = wt + (size_t)n * 8 * cin + c;
+                    mma_bf16(acc[n], a0, a1, a2, a3, ld_pair(wp), ld_pair(wp + 8));
+                }
+            }
+        }
+    }
+    const size_t base = ((size_t)zz * ny + yy) * nx;
+#pragma unroll
+    for (int n = 0; n < COUT / 8; ++n) {
+        const int co = n * 8 + kq;
+        const float b0 = bias ? bias[co] : 0.f, b1 = bias ? bias[co + 1] : 0.f;
+        float v0 = acc[n][0] + b0, v1 = acc[n][1] + b1, v2 = acc[n][2] + b0, v3 = acc[n][3] + b1;
+        if (relu) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); v2 = fmaxf(v2, 0.f); v3 = fmaxf(v3, 0.f); }
+        const int xa = x0 + g, xb = xa + 8;
+        if (xa < nx) *reinterpret_cast<__nv_bfloat162 *>(y + (base + xa) * COUT + co) = __floats2bfloat162_rn(v0, v1);
+        if (xb < nx) *reinterpret_cast<__nv_bfloat162 *>(y + (base + xb) * COUT + co) = __floats2bfloat162_rn(v2, v3);
+    }
+}
+
+// wf[tap][ci][co] = w[26 - tap][co][ci]: kernel of the input gradient
+__global__ void k_flip_weights(int cin, int cout, const bf16 *__restrict__ w, bf16 *__restrict__ wf) {
+    const int n = 27 * cin * cout;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int co = i % cout, ci = (i / cout) % cin, tap = i / (cout * cin);
+        wf[i] = w[((size_t)(26 - tap) * cout + co) * cin + ci];
+    }
+}
+
+// dw[tap][co][ci] += sum_v g[v][co] x[v + off(tap)][ci]; db[co] += sum_v g[v][co].
+// Block: one tap, a run of voxels, a tile of (co, ci); FP32 partial sums, one atomic each.
+constexpr int kWG = 256, kWV = 32;
+__global__ void __launch_bounds__(kWG) k_conv3d_wgrad(int nx, int ny, int nz, int cin, int cout,
+                                                       const bf16 *__restrict__ x, const bf16 *__restrict__ g,
+                                                       float *dw, float *db, int vox_per_block) {
+    extern __shared__ float sh[];
+    float *sg = sh, *sx = sh + kWV * cout;
+    const int tap = blockIdx.y;
+    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    const long long N = (long long)nx * ny * nz;
+    const long long v0 = (long long)blockIdx.x * vox_per_block;
+    const long long v1 = min(N, v0 + vox_per_block);
+    const int pairs = cin * cout;
+    constexpr int kPer = 24;
+    float acc[kPer];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) acc[i] = 0.f;
+    float bacc = 0.f;
+    for (long long vb = v0; vb < v1; vb += kWV) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < kWV * cout; i += blockDim.x) {
+            const long long v = vb + i / cout;
+            sg[i] = v < v1 ? __bfloat162float(g[v * cout + i % cout]) : 0.f;
+        }
+        for (int i = threadIdx.x; i < kWV * cin; i += blockDim.x) {
+            const long long v = vb + i / cin;
+            float val = 0.f;
+            if (v < v1) {
+                const int xx = (int)(v % nx) + dx, yy = (int)((v / nx) % ny) + dy, zz = (int)(v / ((long long)nx * ny)) + dz;
+                if (xx >= 0 && xx < nx && yy >= 0 && yy < ny && zz >= 0 && zz < nz)
+                    val = __bfloat162float(x[(((long long)zz * ny + yy) * nx + xx) * cin + i % cin]);
+            }
+            sx[i] = val;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const int pidx = threadIdx.x + i * kWG;
+            if (pidx < pairs) {
+                const int co = pidx / cin, ci = pidx % cin;
+                float s = acc[i];
+                for (int t = 0; t < kWV; ++t) s = fmaf(sg[t * cout + co], sx[t * cin + ci], s);
+                acc[i] = s;
+            }
+        }
+        if (tap == 13 && threadIdx.x < cout)
+            for (int t = 0; t < kWV; ++t) bacc += sg[t * cout + threadIdx.x];
+    }
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int pidx = threadIdx.x + i * kWG;
+        if (pidx < pairs && acc[i] != 0.f) atomicAdd(dw + (size_t)tap * pairs + pidx, acc[i]);
+    }
+    if (tap == 13 && threadIdx.x < cout && db && bacc != 0.f) atomicAdd(db + threadIdx.x, bacc);
+}
+
+// c = a + b (BF16, FP32 add)
+__global__ void k_add_bf16(long long n, const bf16 *__restrict__ a, const bf16 *__restrict__ b, bf16 *c) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        c[i] = __float2bfloat16(__bfloat162float(a[i]) + __bfloat162float(b[i]));
+}
+
+// g = dout * (act > 0)
+__global__ void k_relu_grad(long long n, const bf16 *__restrict__ act, const bf16 *__restrict__ dout, bf16 *g) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        g[i] = __bfloat162float(act[i]) > 0.f ? dout[i] : __float2bfloat16(0.f);
+}
+
+// 2x2x2 average pooling (channels last); nx, ny, nz of the input, even
+__global__ void k_avgpool2(int nx, int ny, int nz, int c, const bf16 *__restrict__ x, bf16 *__restrict__ y) {
+    const int mx = nx / 2, my = ny / 2, mz = nz / 2;
+    const long long n = (long long)mx * my * mz * c;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int ch = (int)(i % c);
+        const long long v = i / c;
+        const int xx = (int)(v % mx), yy = (int)((v / mx) % my), zz = (int)(v / ((long long)mx * my));
+        float s = 0.f;
+        for (int d = 0; d < 8; ++d)
+            s += __bfloat162float(x[((((long long)(2 * zz + (d >> 2)) * ny + 2 * yy + ((d >> 1) & 1)) * nx + 2 * xx + (d & 1))) * c + ch]);
+        y[i] = __float2bfloat16(0.125f * s);
+    }
+}
+
+// adjoint of avgpool2: dx = dy / 8 spread over the 2x2x2 block
+__global__ void k_avgpool2_grad(int nx, int ny, int nz, int c, const bf16 *__restrict__ dy, bf16 *__restrict__ dx) {
+    const long long n = (long long)nx * ny * nz * c;
+    const int mx = nx / 2, my = ny / 2;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int ch = (int)(i % c);
+        const long long v = i / c;
+        const int xx = (int)(v % nx), yy = (int)((v / nx) % ny), zz = (int)(v / ((long long)nx * ny));
+        dx[i] = __float2bfloat16(0.125f * __bfloat162float(dy[(((long long)(zz / 2) * my + yy / 2) * mx + xx / 2) * c + ch]));
+    }
+}
+
+// nearest 2x upsampling of x (nx, ny, nz: input sizes) into channels [c0, c0 + c) of y (ctot channels)
+__global__ void k_upsample2(int nx, int ny, int nz, int c, const bf16 *__restrict__ x, int ctot, int c0, bf16 *__restrict__ y) {
+    const int ox = 2 * nx, oy = 2 * ny, oz = 2 * nz;
+    const long long n = (long long)ox * oy * oz * c;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int ch = (int)(i % c);
+        const long long v = i / c;
+        const int xx = (int)(v % ox), yy = (int)((v / ox) % oy), zz = (int)(v / ((long long)ox * oy));
+        y[v * ctot + c0 + ch] = x[(((long long)(zz / 2) * ny + yy / 2) * nx + xx / 2) * c + ch];
+    }
+}
+
+// adjoint of upsample2: dx = sum over the 2x2x2 children of channels [c0, c0 + c) of dy
+__global__ void k_upsample2_grad(int nx, int ny, int nz, int c, const bf16 *__restrict__ dy, int ctot, int c0,
+                                 bf16 *__restrict__ dx) {
+    const long long n = (long long)nx * ny * nz * c;
+    const int ox = 2 * nx, oy = 2 * ny;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int ch = (int)(i % c);
+        const long long v = i / c;
+        const int xx = (int)(v % nx), yy = (int)((v / nx) % ny), zz = (int)(v / ((long long)nx * ny));
+        float s = 0.f;
+        for (int d = 0; d < 8; ++d)
+            s += __bfloat162float(dy[((((long long)(2 * zz + (d >> 2)) * oy + 2 * yy + ((d >> 1) & 1)) * ox + 2 * xx + (d & 1))) * ctot + c0 + ch]);
+        dx[i] = __float2bfloat16(s);
+    }
+}
+
+// copy channels [s0, s0 + c) of src (cs channels) to channels [d0, d0 + c) of dst (cd channels)
+__global__ void k_copy_channels(long long nvox, int c, const bf16 *__restrict__ src, int cs, int s0, bf16 *__restrict__ dst,
+                                int cd, int d0) {
+    const long long n = nvox * c;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long v = i / c;
+        const int ch = (int)(i % c);
+        dst[v * cd + d0 + ch] = src[v * cs + s0 + ch];
+    }
+}
+
+// pack a float32 volume scaled by s into channel 0 of a 16-channel BF16 tensor (others zero)
+__global__ void k_pack_input(long long nvox, const float *__restrict__ v, float s, bf16 *__restrict__ x) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nvox * 16; i += (long long)gridDim.x * blockDim.x)
+        x[i] = (i % 16 == 0) ? __float2bfloat16(v[i / 16] * s) : __float2bfloat16(0.f);
+}
+
+// 1x1x1 head: out[v] = b + sum_c w[c] feat[v][c] (float32 out)
+__global__ void k_head(long long nvox, int c, const bf16 *__restrict__ f, const float *__restrict__ w, const float *__restrict__ b,
+                       float *out) {
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x) {
+        float s = b[0];
+        for (int ch = 0; ch < c; ++ch) s = fmaf(w[ch], __bfloat162float(f[v * c + ch]), s);
+        out[v] = s;
+    }
+}
+
+// head backward: df[v][c] = dout[v] w[c]; dw[c] += sum_v dout[v] f[v][c]; db += sum dout
+__global__ void k_head_grad(long long nvox, int c, const bf16 *__restrict__ f, const float *__restrict__ w,
+                            const float *__restrict__ dout, bf16 *df, float *dw, float *db) {
+    float acc[64];
+    for (int ch = 0; ch < c; ++ch) acc[ch] = 0.f;
+    float bacc = 0.f;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x) {
+        const float d = dout[v];
+        bacc += d;
+        for (int ch = 0; ch < c; ++ch) {
+            acc[ch] = fmaf(d, __bfloat162float(f[v * c + ch]), acc[ch]);
+            df[v * c + ch] = __float2bfloat16(d * w[ch]);
+        }
+    }
+    for (int ch = 0; ch < c; ++ch) {
+        float s = acc[ch];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0 && s != 0.f) atomicAdd(dw + ch, s);
+    }
+    for (int o = 16; o > 0; o >>= 1) bacc += __shfl_xor_sync(0xffffffffu, bacc, o);
+    if ((threadIdx.x & 31) == 0 && bacc != 0.f) atomicAdd(db, bacc);
+}
+
+// loss += sum (p - t)^2 / n (double); grad = 2 (p - t) / n
+__global__ void k_mse(long long n, const float *__restrict__ p, const float *__restrict__ t, float *grad, double *loss) {
+    double s = 0.0;
+    const float inv = 2.f / (float)n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float d = p[i] - t[i];
+        s += (double)d * d;
+        grad[i] = inv * d;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(loss, s / (double)n);
+}
+
+// Adam on FP32 master weights; refreshes the BF16 copy (if any)
+__global__ void k_adam(long long n, float *p, const float *__restrict__ g, float *m, float *v, float lr, float b1, float b2,
+                       float eps, float c1, float c2, bf16 *pb) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi, vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi; v[i] = vi;
+        const float w = p[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+        p[i] = w;
+        if (pb) pb[i] = __float2bfloat16(w);
+    }
+}
+
+static unsigned grid1(long long n) { return (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 16)); }
+
+static int launched(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? OAT_OK : set_error(OAT_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace oat
+
+using namespace oat;
+
+extern "C" {
+
+int oat_conv3d_bf16(int nx, int ny, int nz, int cin, int cout, const void *x, const void *w, const float *bias, int relu,
+                    void *y, void *stream) {
+    if (nx < 1 || ny < 1 || nz < 1 || cin < 16 || cin % 16 || !x || !w || !y ||
+        (cout != 16 && cout != 32 && cout != 48 && cout != 64 && cout != 96))
+        return set_error(OAT_ERR_INVALID_ARG, "oat_conv3d_bf16: need cin a multiple of 16, cout in {16, 32, 48, 64, 96}");
+    const dim3 grid((nx + 63) / 64, ny, nz);
+    cudaStream_t s = (cudaStream_t)stream;
+    const bf16 *xb = (const bf16 *)x, *wb = (const bf16 *)w;
+    bf16 *yb = (bf16 *)y;
+    if (cout == 16) k_conv3d<16><<<grid, 128, 0, s>>>(nx, ny, nz, cin, xb, wb, bias, relu, yb);
+    else if (cout == 32) k_conv3d<32><<<grid, 128, 0, s>>>(nx, ny, nz, cin, xb, wb, bias, relu, yb);
+    else if (cout == 48) k_conv3d<48><<<grid, 128, 0, s>>>(nx, ny, nz, cin, xb, wb, bias, relu, yb);
+    else if (cout == 64) k_conv3d<64><<<grid, 128, 0, s>>>(nx, ny, nz, cin, xb, wb, bias, relu, yb);
+    else k_conv3d<96><<<grid, 128, 0, s>>>(nx, ny, nz, cin, xb, wb, bias, relu, yb);
+    return launched("oat_conv3d_bf16");
+}
+
+int oat_conv3d_flip_weights(int cin, int cout, const void *w, void *wf, void *stream) {
+    if (cin < 1 || cout < 1 || !w || !wf) return set_error(OAT_ERR_INVALID_ARG, "oat_conv3d_flip_weights: bad arguments");
+    k_flip_weights<<<grid1(27LL * cin * cout), 256, 0, (cudaStream_t)stream>>>(cin, cout, (const bf16 *)w, (bf16 *)wf);
+    return launched("oat_conv3d_flip_weights");
+}
+
+int oat_conv3d_wgrad(int nx, int ny, int nz, int cin, int cout, const void *x, const void *g, float *dw, float *db,
+                     void *stream) {
+    if (nx < 1 || ny < 1 || nz < 1 || cin < 1 || cout < 1 || cin * cout > 24 * kWG || !x || !g || !dw)
+        return set_error(OAT_ERR_INVALID_ARG, "oat_conv3d_wgrad: bad arguments (cin * cout <= 6144)");
+    const long long N = (long long)nx * ny * nz;
+    const int per = 2048;
+    const dim3 grid((unsigned)((N + per - 1) / per), 27);
+    const size_t smem = sizeof(float) * kWV * (cin + cout);
+    k_conv3d_wgrad<<<grid, kWG, smem, (cudaStream_t)stream>>>(nx, ny, nz, cin, cout, (const bf16 *)x, (const bf16 *)g, dw, db, per);
+    return launched("oat_conv3d_wgrad");
+}
+
+int oat_add_bf16(long long n, const void *a, const void *b, void *c, void *stream) {
+    if (n < 0 || !a || !b || !c) return set_error(OAT_ERR_INVALID_ARG, "oat_add_bf16: bad arguments");
+    k_add_bf16<<<grid1(n), 256, 0, (cudaStream_t)stream>>>(n, (const bf16 *)a, (const bf16 *)b, (bf16 *)c);
+    return launched("oat_add_bf16");
+}
+
+int oat_relu_grad(long long n, const void *act, const void *dout, void *g, void *stream) {
+    if (n < 0 || !act || !dout || !g) return set_error(OAT_ERR_INVALID_ARG, "oat_relu_grad: bad arguments");
+    k_relu_grad<<<grid1(n), 256, 0, (cudaStream_t)stream>>>(n, (const bf16 *)act, (const bf16 *)dout, (bf16 *)g);
+    return launched("oat_relu_grad");
+}
+
+int oat_avgpool2(int nx, int ny, int nz, int c, const void *x, void *y, int backward, void *stream) {
+    if (nx < 2 || ny < 2 || nz < 2 || nx % 2 || ny % 2 || nz % 2 || c < 1 || !x || !y)
+        return set_error(OAT_ERR_INVALID_ARG, "oat_avgpool2: even sizes required");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!backward) k_avgpool2<<<grid1((long long)nx * ny * nz * c / 8), 256, 0, s>>>(nx, ny, nz, c, (const bf16 *)x, (bf16 *)y);
+    else k_avgpool2_grad<<<grid1((long long)nx * ny * nz * c), 256, 0, s>>>(nx, ny, nz, c, (const bf16 *)x, (bf16 *)y);
+    return launched("oat_avgpool2");
+}
+
+int oat_upsample2(int nx, int ny, int nz, int c, const void *x, int ctot, int c0, void *y, int backward, void *stream) {
+    if (nx < 1 || ny < 1 || nz < 1 || c < 1 || c0 < 0 || c0 + c > ctot || !x || !y)
+        return set_error(OAT_ERR_INVALID_ARG, "oat_upsample2: bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!backward) k_upsample2<<<grid1(8LL * nx * ny * nz * c), 256, 0, s>>>(nx, ny, nz, c, (const bf16 *)x, ctot, c0, (bf16 *)y);
+    else k_upsample2_grad<<<grid1((long long)nx * ny * nz * c), 256, 0, s>>>(nx, ny, nz, c, (const bf16 *)x, ctot, c0, (bf16 *)y);
+    return launched("oat_upsample2");
+}
+
+int oat_copy_channels(long long nvox, int c, const void *src, int cs, int s0, void *dst, int cd, int d0, void *stream) {
+    if (nvox < 0 || c < 1 || s0 + c > cs || d0 + c > cd || !src || !dst) return set_error(OAT_ERR_INVALID_ARG, "oat_copy_channels");
+    k_copy_channels<<<grid1(nvox * c), 256, 0, (cudaStream_t)stream>>>(nvox, c, (const bf16 *)src, cs, s0, (bf16 *)dst, cd, d0);
+    return launched("oat_copy_channels");
+}
+
+int oat_pack_input(long long nvox, const float *v, float scale, void *x, void *stream) {
+    if (nvox < 0 || !v || !x) return set_error(OAT_ERR_INVALID_ARG, "oat_pack_input");
+    k_pack_input<<<grid1(nvox * 16), 256, 0, (cudaStream_t)stream>>>(nvox, v, scale, (bf16 *)x);
+    return launched("oat_pack_input");
+}
+
+int oat_head(long long nvox, int c, const void *f, const float *w, const float *b, float *out, void *stream) {
+    if (nvox < 0 || c < 1 || c > 64 || !f || !w || !b || !out) return set_error(OAT_ERR_INVALID_ARG, "oat_head");
+    k_head<<<grid1(nvox), 256, 0, (cudaStream_t)stream>>>(nvox, c, (const bf16 *)f, w, b, out);
+    return launched("oat_head");
+}
+
+int oat_head_grad(long long nvox, int c, const void *f, const float *w, const float *dout, void *df, float *dw, float *db,
+                  void *stream) {
+    if (nvox < 0 || c < 1 || c > 64 || !f || !w || !dout || !df || !dw || !db) return set_error(OAT_ERR_INVALID_ARG, "oat_head_grad");
+    k_head_grad<<<grid1(nvox), 256, 0, (cudaStream_t)stream>>>(nvox, c, (const bf16 *)f, w, dout, (bf16 *)df, dw, db);
+    return launched("oat_head_grad");
+}
+
+int oat_mse(long long n, const float *pred, const float *target, float *grad, double *loss, void *stream) {
+    if (n < 1 || !pred || !target || !grad || !loss) return set_error(OAT_ERR_INVALID_ARG, "oat_mse");
+    k_mse<<<grid1(n), 256, 0, (cudaStream_t)stream>>>(n, pred, target, grad, loss);
+    return launched("oat_mse");
+}
+
+int oat_adam(long long n, float *p, const float *g, float *m, float *v, float lr, float b1, float b2, float eps, int step,
+             void *pbf16, void *stream) {
+    if (n < 0 || !p || !g || !m || !v || step < 1) return set_error(OAT_ERR_INVALID_ARG, "oat_adam");
+    const float c1 = 1.f / (1.f - powf(b1, (float)step)), c2 = 1.f / (1.f - powf(b2, (float)step));
+    k_adam<<<grid1(n), 256, 0, (cudaStream_t)stream>>>(n, p, g, m, v, lr, b1, b2, eps, c1, c2, (bf16 *)pbf16);
+    return launched("oat_adam");
+}
+
+}  // extern "C"
