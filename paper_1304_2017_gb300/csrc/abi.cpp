@@ -104,7 +104,7 @@ int oat_plan_query(oat_plan plan, int want_count, oat_stats *st) {
     st->points_grid = -1;
     st->table_bytes = p->table_bytes;
     st->scratch_bytes = p->scratch_bytes;
-    st->work_items = p->n_items;
+    st->work_items = p->fwd.items;
     if (want_count) {
         DeviceGuard dg(p->device);
         if (dg.err != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_plan_query: ") + cudaGetErrorString(dg.err));

@@ -9,7 +9,8 @@
 // k_brick_gather_t  one thread block per brick of kBA^3 cells (and range of transducers).  The
 //                   block walks, transducer by transducer, the lattice points that can lie in
 //                   the brick (brick.cuh), evaluates each with the lattice-point functions shared
-//                   with the projector, and for the points whose cell lies in the brick adds the
+//                   with the projector (oat_internal.h), and for the points whose cell lies in
+//                   the brick adds the
 //                   eight weights w_c g'_{q,k}, rounded to a fixed-point unit chosen from max|y|,
 //                   to the brick's (kBA+1)^3 node sums with 32-bit integer shared-memory atomics.
 //                   Integer addition is exact and associative, so the sums do not depend on the
@@ -39,7 +40,7 @@ struct AdjArgs {
     int nx, ny, nz, K, Q;
     int nb[3], bs[3];
     int qchunk, kspan, qpass;
-    float O[3];
+    float O[3], O_lo[3];
     float R0, dR;
     float gscale;                 // max |g'| / max |y|
     int apply_d;
@@ -94,12 +95,13 @@ __device__ __forceinline__ void scatter8(int *shi, unsigned int *slo, float4 e, 
 
 template <int B, int DT>
 __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
-    extern __shared__ int shi[];   // (B+1)^3 high halves, (B+1)^3 low halves, ring slots, queues
+    extern __shared__ int shi[];   // (B+1)^3 high halves, (B+1)^3 low halves, segment slots, queues
     constexpr int S1 = B + 1, S2 = (B + 1) * (B + 1), NN = (B + 1) * (B + 1) * (B + 1);
     constexpr int NN2 = 2 * NN + ((2 * NN) & 3 ? 4 - ((2 * NN) & 3) : 0);
     unsigned int *slo = (unsigned int *)(shi + NN);
-    RingSlot *slots = (RingSlot *)(shi + NN2);
+    SegSlot *slots = (SegSlot *)(shi + NN2);
     float4 *queues = (float4 *)(slots + kAdjThreads);
+    BrickView *views = (BrickView *)(queues + kQueue * (kAdjThreads / 32));
     const int nqc = (a.Q + a.qchunk - 1) / a.qchunk;
     const int brick = blockIdx.x / nqc;
     const int q0 = (blockIdx.x % nqc) * a.qchunk;
@@ -121,7 +123,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
     // contributions |w g'| <= max|g'| map to at most 2^30 units
     const float scale = (float)pow2_scale((double)__uint_as_float(*a.amax) * (double)a.gscale, 30);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    RingSlot *ws = slots + warp * 32;
+    SegSlot *ws = slots + warp * 32;
     float4 *wq = queues + warp * kQueue;
     const unsigned lt_mask = (1u << lane) - 1u;
 
@@ -129,10 +131,18 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
         const int qe = min(q1, qp + a.qpass);
         const int units = (qe - qp) * a.kspan;
         int vq = -1;
-        BrickView v;
+        BrickView &v = views[warp];   // the current transducer's view of the brick (shared, per warp)
+        float ex[3], ey[3];
         for (int u = warp; u < units; u += nwarps) {
             const int q = qp + u / a.kspan;
-            if (q != vq) { brick_view(a.t.xd[q], a.O, c, rb, a.R0, a.dR, a.K, v); vq = q; }
+            if (q != vq) {
+                __syncwarp();
+                if (lane == 0) brick_view(a.t.xd[q], a.O, c, rb, a.R0, a.dR, a.K, v);
+                __syncwarp();
+#pragma unroll
+                for (int d = 0; d < 3; ++d) { ex[d] = v.ex[d]; ey[d] = v.ey[d]; }
+                vq = q;
+            }
             const int k = v.k0 + u % a.kspan;
             if (k > v.k1) continue;
             const int ck = v.cls * a.K + k;
@@ -144,32 +154,35 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
             const int off = __ldg(a.t.ring_off + ck);
             int qh = 0, qt = 0;   // queue head and tail (warp-uniform)
             for (int ib = ilo; ib <= ihi; ib += 32) {
-                int nre;
-                const int total = ring_batch(v, a.t.rings, off, ib, ihi, a.O, rb2, blo, bhi, ws, lane, &nre);
-                if (total == 0) continue;
-                const int my_start = lane < nre ? ws[lane].start : 0x7fffffff;
-                for (int f = 0; f < total; f += 32) {
-                    float3 P;
-                    bool own = false;
-                    float4 ent;
-                    if (batch_point(ws, f, lane, my_start, total, v, P)) {
-                        const float fx = floorf(P.x), fy = floorf(P.y), fz = floorf(P.z);
-                        const int lx = (int)fx - L[0], ly = (int)fy - L[1], lz = (int)fz - L[2];
-                        own = (unsigned)lx < (unsigned)E[0] && (unsigned)ly < (unsigned)E[1] && (unsigned)lz < (unsigned)E[2];
-                        ent = make_float4(P.x - fx, P.y - fy, P.z - fz, __int_as_float(lz * S2 + ly * S1 + lx));
-                    }
-                    // queue the owned points; scatter them 32 at a time with every lane busy
-                    const unsigned om = __ballot_sync(0xffffffffu, own);
-                    if (own) wq[(qt + __popc(om & lt_mask)) & (kQueue - 1)] = ent;
-                    qt += __popc(om);
-                    __syncwarp();
-                    if (qt - qh >= 32) {
-                        scatter8<S1, S2>(shi, slo, wq[(qh + lane) & (kQueue - 1)], gq);
-                        qh += 32;
+                int wa0, wna, wb0, wnb, sincl;
+                const int S = ring_windows(v, a.t.rings, off, ib, ihi, a.O, rb2, blo, bhi, lane, wa0, wna, wb0, wnb, sincl);
+                for (int sc = 0; sc < S; sc += 32) {
+                    int my_start;
+                    const int total = segment_chunk(a.t.xd + q, a.t.rings, a.t.anchors, off, ib, a.O, a.O_lo, L, sc, S,
+                                                    lane, wa0, wna, wb0, wnb, sincl, ws, my_start);
+                    for (int f = 0; f < total; f += 32) {
+                        int lc[3];
+                        float w[3];
+                        bool own = false;
+                        float4 ent;
+                        if (segment_point(ws, f, lane, my_start, total, ex, ey, lc, w)) {
+                            own = (unsigned)lc[0] < (unsigned)E[0] && (unsigned)lc[1] < (unsigned)E[1] &&
+                                  (unsigned)lc[2] < (unsigned)E[2];
+                            ent = make_float4(w[0], w[1], w[2], __int_as_float(lc[2] * S2 + lc[1] * S1 + lc[0]));
+                        }
+                        // queue the owned points; scatter them 32 at a time with every lane busy
+                        const unsigned om = __ballot_sync(0xffffffffu, own);
+                        if (own) wq[(qt + __popc(om & lt_mask)) & (kQueue - 1)] = ent;
+                        qt += __popc(om);
                         __syncwarp();
+                        if (qt - qh >= 32) {
+                            scatter8<S1, S2>(shi, slo, wq[(qh + lane) & (kQueue - 1)], gq);
+                            qh += 32;
+                            __syncwarp();
+                        }
                     }
+                    __syncwarp();
                 }
-                __syncwarp();
             }
             if (lane < qt - qh) scatter8<S1, S2>(shi, slo, wq[(qh + lane) & (kQueue - 1)], gq);
             __syncwarp();
@@ -211,7 +224,7 @@ static int backproject_with(Plan &p, const void *data, float *vol, cudaStream_t 
     a.vacc = (unsigned long long *)vacc;
     a.amax = amax;
     a.nx = p.nx; a.ny = p.ny; a.nz = p.nz; a.K = p.K; a.Q = p.Q;
-    for (int d = 0; d < 3; ++d) { a.nb[d] = p.adj.nb[d]; a.bs[d] = p.adj.bs[d]; a.O[d] = p.O[d]; }
+    for (int d = 0; d < 3; ++d) { a.nb[d] = p.adj.nb[d]; a.bs[d] = p.adj.bs[d]; a.O[d] = p.O[d]; a.O_lo[d] = p.O_lo[d]; }
     a.qchunk = p.adj.qchunk; a.kspan = p.adj.kspan; a.qpass = p.adj_qpass;
     a.R0 = p.R0; a.dR = p.dR;
     a.gscale = p.gscale;
@@ -283,7 +296,8 @@ int launch_backproject_static(Plan &p, const void *data, float *vol, cudaStream_
 size_t adjoint_smem_bytes() {
     const size_t nn2 = 2 * (size_t)(kBA + 1) * (kBA + 1) * (kBA + 1);
     const size_t pad = (nn2 & 3) ? 4 - (nn2 & 3) : 0;
-    return sizeof(int) * (nn2 + pad) + sizeof(RingSlot) * kAdjThreads + sizeof(float4) * kQueue * (kAdjThreads / 32);
+    return sizeof(int) * (nn2 + pad) + sizeof(SegSlot) * kAdjThreads + sizeof(float4) * kQueue * (kAdjThreads / 32) +
+           sizeof(BrickView) * (kAdjThreads / 32);
 }
 
 int set_adjoint_attributes() {

@@ -161,66 +161,122 @@ __device__ __forceinline__ bool ring_box_ranges(const BrickView &v, const Ring &
     return true;
 }
 
-// Ring record of a warp's flattened candidate list: ring centre, radius, azimuth step, its
-// index ranges [ja, ja + na) and [jb, ...), and the ring's first position in the list.
-struct RingSlot {
-    float cx, cy, cz, a;
-    float dphi;
-    int ja, na, jb;
-    int start;
-    int pad[3];
+// ---------------------------------------------------------------------------- candidates
+// A warp enumerates the candidates of one (transducer, shell) in three levels:
+//   rings     one lane per ring: its azimuth windows clipped to the brick (ring_windows);
+//   segments  the part of a window that shares one anchor (j >> 5): up to 32 points.  One lane
+//             per segment computes the anchor and fills a slot (segment_chunk);
+//   points    the segments' points spread evenly over the lanes (segment_point).
+
+// One anchor segment of a warp's chunk.
+struct SegSlot {
+    float f[3];          // anchor fraction A - I
+    int I[3];            // anchor cell I, relative to the brick's lowest cell L
+    float xa, ya;        // anchor local coordinates (hi parts)
+    float dphi, dphi_lo;
+    int mp;              // m = j - j_A of the segment's first point | poly << 8
+    int start;           // position of the segment's first point in the chunk's candidate list
 };
 
-// One lane per ring i = ib + lane (i <= ihi) of shell ck: the ring's azimuth windows clipped to the
-// brick, written compacted (non-empty rings only, in ring order) to the warp's slots ws.  Returns
-// the number of candidates of the batch; *nre = number of filled slots.  Warp-collective.
-__device__ __forceinline__ int ring_batch(const BrickView &v, const Ring *__restrict__ rings, int off, int ib, int ihi,
-                                          const float O[3], float rb2, const float blo[3], const float bhi[3],
-                                          RingSlot *ws, int lane, int *nre) {
+__device__ __forceinline__ int anchor_segments(int lo, int n) {
+    return n > 0 ? ((lo + n - 1) >> kAnchorShift) - (lo >> kAnchorShift) + 1 : 0;
+}
+
+// Lane i - ib of rings ib..ihi of shell ck: the ring's windows [wa0, wa0 + wna) and
+// [wb0, wb0 + wnb) clipped to the brick, and the inclusive prefix over lanes of their anchor
+// segments.  Returns the batch's segment count.  Warp-collective.
+__device__ __forceinline__ int ring_windows(const BrickView &v, const Ring *__restrict__ rings, int off, int ib, int ihi,
+                                            const float O[3], float rb2, const float blo[3], const float bhi[3],
+                                            int lane, int &wa0, int &wna, int &wb0, int &wnb, int &sincl) {
     const int i = ib + lane;
     int a0 = 0, a1 = -1, b0 = 0, b1 = -1;
-    Ring r;
-    r.h = 0.f; r.a = 0.f; r.dphi = 0.f; r.nj = 0;
-    float3 Bq = make_float3(0.f, 0.f, 0.f);
     if (i <= ihi) {
-        r = rings[off + i];
-        Bq = ring_base(O, v.ez, r.h);
-        ring_box_ranges(v, r, Bq, rb2, blo, bhi, a0, a1, b0, b1);
+        const Ring r = rings[off + i];
+        ring_box_ranges(v, r, ring_base(O, v.ez, r.h), rb2, blo, bhi, a0, a1, b0, b1);
     }
-    const int na = max(0, a1 - a0 + 1), nb = max(0, b1 - b0 + 1), n = na + nb;
-    const unsigned ne = __ballot_sync(0xffffffffu, n > 0);
-    *nre = __popc(ne);
-    if (ne == 0u) return 0;
-    int incl = n;   // inclusive prefix over lanes
+    wa0 = a0; wna = max(0, a1 - a0 + 1);
+    wb0 = b0; wnb = max(0, b1 - b0 + 1);
+    int incl = anchor_segments(wa0, wna) + anchor_segments(wb0, wnb);
+#pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int t = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += t;
     }
-    if (n > 0) {
-        RingSlot &sl = ws[__popc(ne & ((1u << lane) - 1u))];
-        sl.cx = Bq.x; sl.cy = Bq.y; sl.cz = Bq.z; sl.a = r.a;
-        sl.dphi = r.dphi; sl.ja = a0; sl.na = na; sl.jb = b0; sl.start = incl - n;
+    sincl = incl;
+    return __shfl_sync(0xffffffffu, incl, 31);
+}
+
+// Segments sc .. sc + 31 of the batch, one per lane: anchor and slot ws[lane].  Returns the
+// chunk's number of candidates; my_start = first candidate of slot `lane` (INT_MAX if none).
+// Warp-collective.
+__device__ __forceinline__ int segment_chunk(const Xdcr *__restrict__ xq, const Ring *__restrict__ rings,
+                                             const float4 *__restrict__ anchors, int off, int ib, const float Oh[3],
+                                             const float Ol[3], const int L[3], int sc, int S, int lane, int wa0,
+                                             int wna, int wb0, int wnb, int sincl, SegSlot *ws, int &my_start) {
+    const int g = sc + lane;
+    // owning ring lane: the number of lanes whose inclusive prefix is <= g
+    int r = 0;
+#pragma unroll
+    for (int b = 16; b >= 1; b >>= 1) {
+        const int sv = __shfl_sync(0xffffffffu, sincl, r + b - 1);
+        if (sv <= g) r += b;
     }
+    const int ra0 = __shfl_sync(0xffffffffu, wa0, r), rna = __shfl_sync(0xffffffffu, wna, r);
+    const int rb0 = __shfl_sync(0xffffffffu, wb0, r), rnb = __shfl_sync(0xffffffffu, wnb, r);
+    const int rincl = __shfl_sync(0xffffffffu, sincl, r);
+    int cnt = 0, j0 = 0, t = 0;
+    if (g < S) {
+        const int nsa = anchor_segments(ra0, rna), nsb = anchor_segments(rb0, rnb);
+        const int sg = g - (rincl - nsa - nsb);
+        int lo, hi;
+        if (sg < nsa) { t = (ra0 >> kAnchorShift) + sg; lo = ra0; hi = ra0 + rna - 1; }
+        else { t = (rb0 >> kAnchorShift) + (sg - nsa); lo = rb0; hi = rb0 + rnb - 1; }
+        j0 = max(lo, t << kAnchorShift);
+        cnt = min(hi, (t << kAnchorShift) + kAnchorMask) - j0 + 1;
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (cnt > 0) {
+        const Ring rg = rings[off + ib + r];
+        const float4 xy = __ldg(anchors + rg.aoff + t);
+        int I[3];
+        float fr[3];
+        anchor_point(Oh, Ol, *xq, rg.h, rg.h_lo, xy, I, fr);
+        SegSlot &sl = ws[lane];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) { sl.f[d] = fr[d]; sl.I[d] = I[d] - L[d]; }
+        sl.xa = xy.x; sl.ya = xy.z;
+        sl.dphi = rg.dphi; sl.dphi_lo = rg.dphi_lo;
+        sl.mp = (j0 - (t << kAnchorShift)) | (rg.poly << 8);
+        sl.start = incl - cnt;
+    }
+    my_start = cnt > 0 ? incl - cnt : 0x7fffffff;
     __syncwarp();
     return __shfl_sync(0xffffffffu, incl, 31);
 }
 
-// Candidate f + lane of a ring batch (my_start: start of slot `lane`, or INT_MAX): its lattice
-// point, through the same functions in both directions.  Warp-collective; returns false for
-// lanes past the end of the list.
-__device__ __forceinline__ bool batch_point(const RingSlot *ws, int f, int lane, int my_start, int total,
-                                            const BrickView &v, float3 &P) {
+// Candidate f + lane of a chunk: its cell relative to the brick's lowest cell (lc) and its
+// position in that cell (w), through the shared lattice-point functions (ex, ey: the
+// transducer's frame, hi parts).  Warp-collective;
+// returns false for lanes past the end of the list.
+__device__ __forceinline__ bool segment_point(const SegSlot *ws, int f, int lane, int my_start, int total,
+                                              const float ex[3], const float ey[3], int lc[3], float w[3]) {
     const int before = __popc(__ballot_sync(0xffffffffu, my_start <= f));
     const unsigned inside =
         __reduce_or_sync(0xffffffffu, (my_start > f && my_start < f + 32) ? (1u << (my_start - f)) : 0u);
     const int cidx = f + lane;
     if (cidx >= total) return false;
-    const RingSlot sl = ws[before - 1 + __popc(inside & ((2u << lane) - 1u))];
-    const int o2 = cidx - sl.start;
-    const int j = o2 < sl.na ? sl.ja + o2 : sl.jb + (o2 - sl.na);
-    float uu, vv;
-    ring_uv(sl.a, sl.dphi, j, uu, vv);
-    P = ring_point(make_float3(sl.cx, sl.cy, sl.cz), v.ex, v.ey, uu, vv);
+    const SegSlot &sl = ws[before - 1 + __popc(inside & ((2u << lane) - 1u))];
+    const int mp = sl.mp;
+    const float3 R = anchor_offset(sl.f, sl.xa, sl.ya, ex, ey, sl.dphi, sl.dphi_lo, mp >> 8,
+                                   (mp & 0xff) + (cidx - sl.start));
+    const float fx = floorf(R.x), fy = floorf(R.y), fz = floorf(R.z);
+    lc[0] = sl.I[0] + (int)fx; lc[1] = sl.I[1] + (int)fy; lc[2] = sl.I[2] + (int)fz;
+    w[0] = __fsub_rn(R.x, fx); w[1] = __fsub_rn(R.y, fy); w[2] = __fsub_rn(R.z, fz);
     return true;
 }
 

@@ -1,11 +1,11 @@
 // Projector u = D G alpha (Eqs. dis_srt and dis_g2p).
 //
-// k_radial_gather  G alpha into an FP64 scratch [Q][K]: radial-lane shell gather (below).
-// k_apply_d_dbl    u_k = C_D (g_{k+1}/tau_{k+1} - g_{k-1}/tau_{k-1}) for 1 <= k <= K-2, 0 at the
+// k_brick_gather   G alpha as 64-bit fixed-point sums [Q][K]: per-brick shell gather (below).
+// k_apply_d_fix    u_k = C_D (g_{k+1}/tau_{k+1} - g_{k-1}/tau_{k-1}) for 1 <= k <= K-2, 0 at the
 //                  ends (or u = g without D) in double precision -- the difference of
 //                  neighbouring samples cancels by one to three digits -- with one rounding to
 //                  float32 / float16 / bfloat16 at the end.
-// k_absmax         max |x| of a buffer (the backprojector's fixed-point unit).
+// k_absmax         max |x| of a buffer (the fixed-point units of both directions).
 // k_count          lattice points whose stencil touches the grid (oat_plan_query).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -32,126 +32,6 @@ __global__ void k_absmax(const void *__restrict__ x, size_t n, int dtype, unsign
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
 }
 
-// ---------------------------------------------------------------------------- radial lanes
-// k_radial_gather: one block per (radius class, block of 32 consecutive shells, up to kRT
-// transducers of the class).  Lane l of every warp owns shell kb + l; warps split the rings.
-// For ring i and azimuth index j all 32 lanes evaluate the lattice points (kb + l, i, j), which
-// lie along a short radial segment (consecutive shells are c dt apart), so the eight-node
-// gathers of one warp instruction fall on few cache lines; (cos phi_j, sin phi_j) of a lane is
-// shared by the kRT transducers.  Every (q, k) is owned by one block: the double-precision sum
-// is written once, without atomics.
-constexpr int kRT = 8;
-constexpr int kRWarps = 8;
-
-struct RadArgs {
-    DevTables t;
-    const int4 *items;      // (class, first shell, first in qlist, count)
-    const float *vol;
-    double *g;
-    int nx, ny, nz, K;
-    float O[3];
-    float ds2;
-};
-
-__global__ void __launch_bounds__(kRWarps * 32, 3) k_radial_gather(RadArgs a) {
-    const int4 it = a.items[blockIdx.x];
-    const int cls = it.x, kb = it.y, q0 = it.z, nq = it.w;
-    __shared__ float sE[kRT][9];
-    __shared__ float2 sRed[kRWarps][kRT][32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x < kRT * 9) {
-        const int t = threadIdx.x / 9, c = threadIdx.x % 9;
-        float v = 0.f;
-        if (t < nq) {
-            const Xdcr &x = a.t.xd[a.t.qlist[q0 + t]];
-            v = c < 3 ? x.ex[c] : (c < 6 ? x.ey[c - 3] : x.ez[c - 6]);
-        }
-        sE[t][c] = v;
-    }
-    __syncthreads();
-    const int k = kb + lane;
-    const bool kval = k < a.K;
-    const int ck = cls * a.K + (kval ? k : 0);
-    const int nr = kval ? __ldg(a.t.ring_cnt + ck) : 0;
-    const int off = kval ? __ldg(a.t.ring_off + ck) : 0;
-    int nrmax = nr;
-    for (int o = 16; o > 0; o >>= 1) nrmax = max(nrmax, __shfl_xor_sync(0xffffffffu, nrmax, o));
-    const float bx = (float)a.nx, by = (float)a.ny, bz = (float)a.nz;
-    float tot[kRT], err[kRT];
-#pragma unroll
-    for (int t = 0; t < kRT; ++t) { tot[t] = 0.f; err[t] = 0.f; }
-
-    for (int i = warp; i < nrmax; i += kRWarps) {
-        Ring r;
-        if (i < nr) r = a.t.rings[off + i];
-        else { r.h = 0.f; r.a = 0.f; r.dphi = 0.f; r.nj = 0; }
-        int njmax = r.nj;
-        for (int o = 16; o > 0; o >>= 1) njmax = max(njmax, __shfl_xor_sync(0xffffffffu, njmax, o));
-        if (njmax == 0) continue;
-        float3 B[kRT];
-#pragma unroll
-        for (int t = 0; t < kRT; ++t) B[t] = ring_base(a.O, &sE[t][6], r.h);
-        for (int j0 = 0; j0 < njmax; j0 += 16) {
-            // skip the 16-point segments that cannot reach the grid (box [-1, n)^3 grown by the
-            // segment's half arc length and one spacing), per transducer
-            unsigned act = 0u;
-            {
-                const bool lv = j0 < r.nj;
-                float cu = 0.f, cv = 0.f;
-                if (lv) {
-                    const float jm = 0.5f * (float)(j0 + min(j0 + 15, r.nj - 1));
-                    float sn, cs;
-                    sincosf(jm * r.dphi, &sn, &cs);
-                    cu = r.a * cs; cv = r.a * sn;
-                }
-                const float reach = 9.0f;
-#pragma unroll
-                for (int t = 0; t < kRT; ++t) {
-                    bool hit = false;
-                    if (lv && t < nq) {
-                        const float3 C = ring_point(B[t], &sE[t][0], &sE[t][3], cu, cv);
-                        const float dx = fmaxf(fmaxf(-1.f - C.x, C.x - bx), 0.f);
-                        const float dy = fmaxf(fmaxf(-1.f - C.y, C.y - by), 0.f);
-                        const float dz = fmaxf(fmaxf(-1.f - C.z, C.z - bz), 0.f);
-                        hit = dx * dx + dy * dy + dz * dz <= reach * reach;
-                    }
-                    if (__any_sync(0xffffffffu, hit)) act |= 1u << t;
-                }
-            }
-            if (act == 0u) continue;
-            const int jend = min(j0 + 16, njmax);
-            for (int j = j0; j < jend; ++j) {
-                if (j < r.nj) {
-                    float u, v;
-                    ring_uv(r, j, u, v);
-#pragma unroll
-                    for (int t = 0; t < kRT; ++t) {
-                        if (act & (1u << t)) {
-                            const float3 P = ring_point(B[t], &sE[t][0], &sE[t][3], u, v);
-                            kadd(tot[t], err[t], trilinear(a.vol, a.nx, a.ny, a.nz, P));
-                        }
-                    }
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int t = 0; t < kRT; ++t) sRed[warp][t][lane] = make_float2(tot[t], err[t]);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < kRT * 32; idx += blockDim.x) {
-        const int t = idx / 32, l = idx % 32;
-        const int kk = kb + l;
-        if (t >= nq || kk >= a.K) continue;
-        float s = 0.f, e = 0.f;
-        for (int w = 0; w < kRWarps; ++w) { kadd(s, e, sRed[w][t][l].x); e += sRed[w][t][l].y; }
-        const int q = a.t.qlist[q0 + t];
-        a.g[(size_t)q * a.K + kk] = (double)a.ds2 * ((double)s + (double)e);
-    }
-}
-
-template <int DT, bool APPLY_D>
-__global__ void k_apply_d_dbl(const double *__restrict__ g, const double *__restrict__ wD, void *out, int Q, int K);
-
 template <int DT>
 __device__ __forceinline__ void store_data(void *out, size_t i, float v) {
     if (DT == OAT_F32) ((float *)out)[i] = v;
@@ -159,62 +39,13 @@ __device__ __forceinline__ void store_data(void *out, size_t i, float v) {
     else ((__nv_bfloat16 *)out)[i] = __float2bfloat16_rn(v);
 }
 
-template <int DT, bool APPLY_D>
-__global__ void k_apply_d_dbl(const double *__restrict__ g, const double *__restrict__ wD, void *out, int Q, int K) {
-    const size_t n = (size_t)Q * K;
-    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(idx % K);
-        double v;
-        if (!APPLY_D) v = g[idx];
-        else if (k < 1 || k > K - 2) v = 0.0;
-        else v = wD[k + 1] * g[idx + 1] - wD[k - 1] * g[idx - 1];
-        store_data<DT>(out, idx, (float)v);
-    }
-}
-
-static int launch_project_radial(Plan &p, const float *vol, void *data, cudaStream_t s) {
-    RadArgs a;
-    a.t = p.t; a.items = p.d_ritems; a.vol = vol; a.g = (double *)p.d_gacc;
-    a.nx = p.nx; a.ny = p.ny; a.nz = p.nz; a.K = p.K;
-    for (int d = 0; d < 3; ++d) a.O[d] = p.O[d];
-    a.ds2 = p.ds2;
-    // shells without lattice points belong to no work item: clear their sums
-    cudaError_t e0 = cudaMemsetAsync(p.d_gacc, 0, sizeof(double) * (size_t)p.Q * p.K, s);
-    if (e0 != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_project: memset: ") + cudaGetErrorString(e0));
-    const bool prof = p.profiling && p.ev_used[0] + 2 <= (int)p.ev[0].size();
-    if (prof) cudaEventRecord(p.ev[0][p.ev_used[0]], s);
-    k_radial_gather<<<(unsigned)p.n_ritems, kRWarps * 32, 0, s>>>(a);
-    if (prof) { cudaEventRecord(p.ev[0][p.ev_used[0] + 1], s); p.ev_used[0] += 2; }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_project: k_radial_gather: ") + cudaGetErrorString(e));
-    const size_t n = (size_t)p.Q * p.K;
-    const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
-    const int dt = p.g.data_dtype;
-    const double *g = (const double *)p.d_gacc;
-#define OAT_APPLY(DTV, AD) k_apply_d_dbl<DTV, AD><<<blocks, 256, 0, s>>>(g, p.t.wD64, data, p.Q, p.K)
-    if (p.g.apply_d) {
-        if (dt == OAT_F32) OAT_APPLY(OAT_F32, true); else if (dt == OAT_F16) OAT_APPLY(OAT_F16, true); else OAT_APPLY(OAT_BF16, true);
-    } else {
-        if (dt == OAT_F32) OAT_APPLY(OAT_F32, false); else if (dt == OAT_F16) OAT_APPLY(OAT_F16, false); else OAT_APPLY(OAT_BF16, false);
-    }
-#undef OAT_APPLY
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_project: k_apply_d: ") + cudaGetErrorString(e));
-    return OAT_OK;
-}
-
-static int launch_project_brick(Plan &p, const float *vol, void *data, cudaStream_t s);
-
-int launch_project(Plan &p, const float *vol, void *data, cudaStream_t s) {
-    return p.fwd_radial ? launch_project_radial(p, vol, data, s) : launch_project_brick(p, vol, data, s);
-}
-
 // ---------------------------------------------------------------------------- bricks
 // k_brick_gather: one block per work item (brick of kBF^3 cells, range of transducers).  The
 // brick's (kBF+1)^3 nodes are staged in shared memory (zero outside the grid).  A warp takes one
 // (transducer, shell) unit at a time; one lane per ring computes the ring's azimuth window
-// clipped to the brick, the candidates are spread evenly over the lanes (brick.cuh), and each
-// point whose cell floor(P) lies in the brick is interpolated from shared memory.  The unit's
+// clipped to the brick, one lane per anchor segment computes its anchor, the candidates are
+// spread evenly over the lanes (brick.cuh), and each point whose cell lies in the brick is
+// interpolated from shared memory.  The unit's
 // compensated FP32 sum is added to g[q][k] as a 64-bit fixed-point integer (one atomic per unit),
 // so the total does not depend on the order in which bricks finish.
 constexpr int kFwdThreads = 1024;
@@ -227,17 +58,18 @@ struct FwdArgs {
     int nx, ny, nz, K, Q;
     int nb[3], bs[3];
     int qchunk, kspan;
-    float O[3];
+    float O[3], O_lo[3];
     float R0, dR;
     double bound_pts;             // max lattice points of one shell
 };
 
 template <int B>
 __global__ void __launch_bounds__(kFwdThreads, 1) k_brick_gather(FwdArgs a) {
-    extern __shared__ float sv[];   // (B+1)^3 nodes of the brick, then the warps' ring slots
+    extern __shared__ float sv[];   // (B+1)^3 nodes of the brick, then the warps' segment slots
     constexpr int S1 = B + 1, S2 = (B + 1) * (B + 1), NN = (B + 1) * (B + 1) * (B + 1);
     constexpr int NNp = NN + ((NN & 3) ? 4 - (NN & 3) : 0);
-    RingSlot *slots = (RingSlot *)(sv + NNp);
+    SegSlot *slots = (SegSlot *)(sv + NNp);
+    BrickView *views = (BrickView *)(slots + kFwdThreads);
     const int nqc = (a.Q + a.qchunk - 1) / a.qchunk;
     const int brick = blockIdx.x / nqc;
     const int q0 = (blockIdx.x % nqc) * a.qchunk;
@@ -262,14 +94,22 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_brick_gather(FwdArgs a) {
     const float rb2 = rb * rb;
     const double scale = pow2_scale(a.bound_pts * (double)__uint_as_float(*a.amax), 61);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    RingSlot *ws = slots + warp * 32;
+    SegSlot *ws = slots + warp * 32;
     const int units = (q1 - q0) * a.kspan;
     int vq = -1;
-    BrickView v;
+    BrickView &v = views[warp];   // the current transducer's view of the brick (shared, per warp)
+    float ex[3], ey[3];
 
     for (int u = warp; u < units; u += nwarps) {
         const int q = q0 + u / a.kspan;
-        if (q != vq) { brick_view(a.t.xd[q], a.O, c, rb, a.R0, a.dR, a.K, v); vq = q; }
+        if (q != vq) {
+            __syncwarp();
+            if (lane == 0) brick_view(a.t.xd[q], a.O, c, rb, a.R0, a.dR, a.K, v);
+            __syncwarp();
+#pragma unroll
+            for (int d = 0; d < 3; ++d) { ex[d] = v.ex[d]; ey[d] = v.ey[d]; }
+            vq = q;
+        }
         const int k = v.k0 + u % a.kspan;
         if (k > v.k1) continue;
         const int ck = v.cls * a.K + k;
@@ -279,24 +119,25 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_brick_gather(FwdArgs a) {
         const int off = __ldg(a.t.ring_off + ck);
         float acc = 0.f, err = 0.f;
         for (int ib = ilo; ib <= ihi; ib += 32) {
-            int nre;
-            const int total = ring_batch(v, a.t.rings, off, ib, ihi, a.O, rb2, blo, bhi, ws, lane, &nre);
-            if (total == 0) continue;
-            const int my_start = lane < nre ? ws[lane].start : 0x7fffffff;
-            for (int f = 0; f < total; f += 32) {
-                float3 P;
-                if (!batch_point(ws, f, lane, my_start, total, v, P)) continue;
-                const float fx = floorf(P.x), fy = floorf(P.y), fz = floorf(P.z);
-                const int lx = (int)fx - L[0], ly = (int)fy - L[1], lz = (int)fz - L[2];
-                if ((unsigned)lx < (unsigned)E[0] && (unsigned)ly < (unsigned)E[1] && (unsigned)lz < (unsigned)E[2]) {
-                    const float wx = P.x - fx, wy = P.y - fy, wz = P.z - fz;
-                    const float *sp = sv + lz * S2 + ly * S1 + lx;
-                    const float c00 = lerp1(sp[0], sp[1], wx), c01 = lerp1(sp[S1], sp[S1 + 1], wx);
-                    const float c10 = lerp1(sp[S2], sp[S2 + 1], wx), c11 = lerp1(sp[S2 + S1], sp[S2 + S1 + 1], wx);
-                    kadd(acc, err, lerp1(lerp1(c00, c01, wy), lerp1(c10, c11, wy), wz));
+            int wa0, wna, wb0, wnb, sincl;
+            const int S = ring_windows(v, a.t.rings, off, ib, ihi, a.O, rb2, blo, bhi, lane, wa0, wna, wb0, wnb, sincl);
+            for (int sc = 0; sc < S; sc += 32) {
+                int my_start;
+                const int total = segment_chunk(a.t.xd + q, a.t.rings, a.t.anchors, off, ib, a.O, a.O_lo, L, sc, S, lane,
+                                                wa0, wna, wb0, wnb, sincl, ws, my_start);
+                for (int f = 0; f < total; f += 32) {
+                    int lc[3];
+                    float w[3];
+                    if (!segment_point(ws, f, lane, my_start, total, ex, ey, lc, w)) continue;
+                    if ((unsigned)lc[0] < (unsigned)E[0] && (unsigned)lc[1] < (unsigned)E[1] && (unsigned)lc[2] < (unsigned)E[2]) {
+                        const float *sp = sv + lc[2] * S2 + lc[1] * S1 + lc[0];
+                        const float c00 = lerp1(sp[0], sp[1], w[0]), c01 = lerp1(sp[S1], sp[S1 + 1], w[0]);
+                        const float c10 = lerp1(sp[S2], sp[S2 + 1], w[0]), c11 = lerp1(sp[S2 + S1], sp[S2 + S1 + 1], w[0]);
+                        kadd(acc, err, lerp1(lerp1(c00, c01, w[1]), lerp1(c10, c11, w[1]), w[2]));
+                    }
                 }
+                __syncwarp();
             }
-            __syncwarp();
         }
         for (int o = 16; o > 0; o >>= 1) {
             const float s2 = __shfl_xor_sync(0xffffffffu, acc, o);
@@ -329,7 +170,8 @@ __global__ void k_apply_d_fix(const long long *__restrict__ gacc, const double *
 
 size_t forward_smem_bytes() {
     const size_t nn = (size_t)(kBF + 1) * (kBF + 1) * (kBF + 1);
-    return sizeof(float) * (nn + ((nn & 3) ? 4 - (nn & 3) : 0)) + sizeof(RingSlot) * kFwdThreads;
+    return sizeof(float) * (nn + ((nn & 3) ? 4 - (nn & 3) : 0)) + sizeof(SegSlot) * kFwdThreads +
+           sizeof(BrickView) * (kFwdThreads / 32);
 }
 
 int set_forward_attributes() {
@@ -338,7 +180,7 @@ int set_forward_attributes() {
     return e == cudaSuccess ? OAT_OK : set_error(OAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
 }
 
-static int launch_project_brick(Plan &p, const float *vol, void *data, cudaStream_t s) {
+int launch_project(Plan &p, const float *vol, void *data, cudaStream_t s) {
     const size_t N = (size_t)p.nx * p.ny * p.nz;
     cudaError_t e = cudaMemsetAsync(p.d_amax, 0, sizeof(unsigned int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p.d_gacc, 0, sizeof(long long) * (size_t)p.Q * p.K, s);
@@ -349,7 +191,7 @@ static int launch_project_brick(Plan &p, const float *vol, void *data, cudaStrea
     a.gacc = (unsigned long long *)p.d_gacc;
     a.amax = p.d_amax;
     a.nx = p.nx; a.ny = p.ny; a.nz = p.nz; a.K = p.K; a.Q = p.Q;
-    for (int d = 0; d < 3; ++d) { a.nb[d] = p.fwd.nb[d]; a.bs[d] = p.fwd.bs[d]; a.O[d] = p.O[d]; }
+    for (int d = 0; d < 3; ++d) { a.nb[d] = p.fwd.nb[d]; a.bs[d] = p.fwd.bs[d]; a.O[d] = p.O[d]; a.O_lo[d] = p.O_lo[d]; }
     a.qchunk = p.fwd.qchunk; a.kspan = p.fwd.kspan;
     a.R0 = p.R0; a.dR = p.dR;
     a.bound_pts = (double)p.max_shell_points;
@@ -378,35 +220,45 @@ static int launch_project_brick(Plan &p, const float *vol, void *data, cudaStrea
 
 // ---------------------------------------------------------------------------- point counting
 
-__global__ void k_count(RadArgs a, unsigned long long *count) {
-    // every lattice point of every (q, k) with its stencil touching the grid
+struct CountArgs {
+    DevTables t;
+    int nx, ny, nz, K;
+    float O[3], O_lo[3];
+};
+
+__global__ void k_count(CountArgs a, unsigned long long *count) {
+    // every lattice point of every (q, k) with its stencil touching the grid, i.e. its cell in
+    // [-1, n-1]^3; a warp takes 32 consecutive points (one anchor) of a ring at a time
     const int qk = blockIdx.x;
     const int q = qk / a.K, k = qk % a.K;
     const Xdcr &x = a.t.xd[q];
     const int ck = x.cls * a.K + k;
     const int nr = a.t.ring_cnt[ck], off = a.t.ring_off[ck];
+    const int lane = threadIdx.x & 31;
     unsigned long long n = 0;
     for (int i = threadIdx.x >> 5; i < nr; i += blockDim.x >> 5) {
         const Ring r = a.t.rings[off + i];
-        const float3 B = ring_base(a.O, x.ez, r.h);
-        for (int j = threadIdx.x & 31; j < r.nj; j += 32) {
-            float u, v;
-            ring_uv(r, j, u, v);
-            const float3 P = ring_point(B, x.ex, x.ey, u, v);
-            n += (P.x >= -1.f && P.x < (float)a.nx && P.y >= -1.f && P.y < (float)a.ny && P.z >= -1.f &&
-                  P.z < (float)a.nz);
+        for (int j0 = 0; j0 < r.nj; j0 += 32) {
+            int I[3];
+            float f[3];
+            anchor_point(a.O, a.O_lo, x, r.h, r.h_lo, a.t.anchors[r.aoff + (j0 >> kAnchorShift)], I, f);
+            if (j0 + lane >= r.nj) continue;
+            const float3 R = anchor_offset(f, a.t.anchors[r.aoff + (j0 >> kAnchorShift)].x,
+                                           a.t.anchors[r.aoff + (j0 >> kAnchorShift)].z, x.ex, x.ey, r.dphi, r.dphi_lo,
+                                           r.poly, lane);
+            const int cx = I[0] + (int)floorf(R.x), cy = I[1] + (int)floorf(R.y), cz = I[2] + (int)floorf(R.z);
+            n += (cx >= -1 && cx < a.nx && cy >= -1 && cy < a.ny && cz >= -1 && cz < a.nz);
         }
     }
     for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
-    if ((threadIdx.x & 31) == 0 && n) atomicAdd(count, n);
+    if (lane == 0 && n) atomicAdd(count, n);
 }
 
 int count_grid_points(Plan &p, long long *out) {
-    RadArgs a;
-    a.t = p.t; a.items = nullptr; a.vol = nullptr; a.g = nullptr;
+    CountArgs a;
+    a.t = p.t;
     a.nx = p.nx; a.ny = p.ny; a.nz = p.nz; a.K = p.K;
-    for (int d = 0; d < 3; ++d) a.O[d] = p.O[d];
-    a.ds2 = p.ds2;
+    for (int d = 0; d < 3; ++d) { a.O[d] = p.O[d]; a.O_lo[d] = p.O_lo[d]; }
     unsigned long long *d = (unsigned long long *)p.d_count;
     cudaError_t e = cudaMemset(d, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) {

@@ -24,14 +24,25 @@ namespace oat {
 //   P = O + h e_z + a (cos(j dphi) e_x + sin(j dphi) e_y)     (index units)
 // where O = -origin / Delta_s is the global origin in index coordinates and
 // (e_x, e_y, e_z) is the transducer's local frame (Appendix).
+//
+// h and dphi are also kept as unevaluated sums of two floats (hi + lo, |lo| <= ulp(hi) / 2),
+// for the anchors below.  Anchor t of the ring is the point j = 32 t; its local coordinates
+// (a cos(32 t dphi), a sin(32 t dphi)) are table entries aoff + t, also as float pairs.
+constexpr int kAnchorShift = 5;                      // one anchor every 32 points of a ring
+constexpr int kAnchorMask = (1 << kAnchorShift) - 1;
+
 struct Ring {
     float h, a, dphi;
     int nj;
+    float h_lo, dphi_lo;
+    int aoff;                 // first anchor of the ring in the anchor table
+    int poly;                 // 1: offsets by Taylor polynomials (32 dphi <= 1), 0: by sincosf
 };
 
-// Per-transducer record: local frame and |r_q| / Delta_s, and its radius class.
+// Per-transducer record: local frame (float pairs hi + lo) and |r_q| / Delta_s, radius class.
 struct Xdcr {
     float ex[3], ey[3], ez[3];
+    float ex_lo[3], ey_lo[3], ez_lo[3];
     float dist;   // |r_q| / Delta_s
     int cls;
     int pad[2];
@@ -43,7 +54,7 @@ struct DevTables {
     const int *ring_cnt;      // [n_cls * K] N_i(class, k)
     const Xdcr *xd;           // [Q]
     const int *qlist;         // transducers sorted by class
-    const int4 *items;        // forward work items (class, k, first in qlist, count)
+    const float4 *anchors;    // (x hi, x lo, y hi, y lo) local coordinates of every anchor
     const float *Rk;          // [K] rho_k / Delta_s (may be <= 0)
     const float *wD;          // [K] C_D / tau_k, 0 where tau_k <= 0
     const double *wD64;       // [K] the same in double (forward D)
@@ -70,17 +81,15 @@ struct Plan {
     int Q = 0, K = 0, n_cls = 0;
     int nx = 0, ny = 0, nz = 0;
     double R = 0, dt = 0, cd = 0;
-    float O[3] = {0, 0, 0};      // -origin / Delta_s
+    float O[3] = {0, 0, 0};      // -origin / Delta_s (hi part)
+    float O_lo[3] = {0, 0, 0};   // its lo part
     float ds2 = 0;               // Delta_s^2
     float R0 = 0, dR = 0;        // rho_0 / Delta_s and c dt / Delta_s
-    long long n_rings = 0, points_ball = 0, n_items = 0;
+    long long n_rings = 0, n_anchors = 0, points_ball = 0;
     long long max_shell_points = 0;   // largest N_i-ring lattice of one shell (fixed-point bound)
     float gscale = 1.f;               // max |g'| / max |y|: 2 max_k C_D/tau_k with D, 1 without
     int adj_qpass = 1;                // transducers per backprojector pass (bounds the 32-bit halves)
     BrickCfg fwd, adj;                 // brick tilings of the projector and the backprojector
-    bool fwd_radial = false;           // projector kernel: radial lanes or bricks
-    const int4 *d_ritems = nullptr;    // radial work items (class, first shell, first in qlist, count)
-    long long n_ritems = 0;
     long long table_bytes = 0, scratch_bytes = 0;
     std::vector<long long> cls_points;   // [n_cls * K] points per (class, k)
 
@@ -123,63 +132,103 @@ constexpr int kMaxEvents = 4096;
 #ifdef __CUDACC__
 namespace oat {
 
-// (u, v) = a (cos phi_j, sin phi_j), phi_j = j * dphi in FP32.  Explicitly rounded so that
-// every kernel evaluates exactly the same values.
-__device__ __forceinline__ void ring_uv(float a, float dphi, int j, float &u, float &v) {
-    float phi = __fmul_rn(__int2float_rn(j), dphi);
-    float s, c;
-    sincosf(phi, &s, &c);
-    u = __fmul_rn(a, c);
-    v = __fmul_rn(a, s);
+// ---------------------------------------------------------------------------- lattice points
+// Every kernel computes lattice point (q, k, i, j) with the functions below, operation for
+// operation, so that a point has the same cell and the same weights in H and in H^T and in
+// every brick that looks at it.
+//
+// FP32 coordinates of magnitude |O| + |h| + a (several hundred grid units when the scanner is
+// far from the grid) would carry rounding errors of ~1e-5 cells.  Instead each point is taken
+// relative to its ring's anchor j_A = 32 floor(j / 32):
+//   anchor  A = O + h e_z + x_A e_x + y_A e_y   in float-pair arithmetic (about 44 bits), split
+//           into its cell I = floor(A) and fraction f = A - I;
+//   point   P - I = f + dx e_x + dy e_y, with (dx, dy) the change of the local coordinates from
+//           the anchor to point j: a rotation by delta = (j - j_A) dphi,
+//             dx = x_A (cos delta - 1) - y_A sin delta,  dy = y_A (cos delta - 1) + x_A sin delta,
+//           in FP32 (|dx|, |dy| <= 32 grid units).
+// The cell of P is I + floor(P - I): it depends only on (q, k, i, j).
+
+// s + e = a + b exactly (Knuth's two-sum).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-__device__ __forceinline__ void ring_uv(const Ring &r, int j, float &u, float &v) { ring_uv(r.a, r.dphi, j, u, v); }
+// (s + e) += (xh + xl)(yh + yl), dropping xl yl: the product's rounding error comes from an FMA.
+__device__ __forceinline__ void pair_madd(float xh, float xl, float yh, float yl, float &s, float &e) {
+    const float p = __fmul_rn(xh, yh);
+    const float pe = fmaf(xl, yh, fmaf(xh, yl, fmaf(xh, yh, -p)));
+    float t;
+    two_sum(s, p, s, t);
+    e = __fadd_rn(e, __fadd_rn(t, pe));
+}
 
-// Ring centre in index coordinates for one transducer: B = O + h e_z.
+// Anchor of a ring for transducer x: local coordinates xy = (x hi, x lo, y hi, y lo), ring axial
+// offset (hh, hl); O = (Oh, Ol).  Returns the cell I and the fraction f (f may leave [0, 1) by
+// the size of the pair's low part).
+__device__ __forceinline__ void anchor_point(const float Oh[3], const float Ol[3], const Xdcr &x, float hh, float hl,
+                                             float4 xy, int I[3], float f[3]) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        float s = Oh[d], e = Ol[d];
+        pair_madd(hh, hl, x.ez[d], x.ez_lo[d], s, e);
+        pair_madd(xy.x, xy.y, x.ex[d], x.ex_lo[d], s, e);
+        pair_madd(xy.z, xy.w, x.ey[d], x.ey_lo[d], s, e);
+        const float fl = floorf(s);
+        I[d] = (int)fl;
+        f[d] = __fadd_rn(__fsub_rn(s, fl), e);
+    }
+}
+
+// sin(d) and cos(d) - 1 for |d| <= 1 from their Taylor series (through d^11 and d^12: the
+// first omitted terms are below 2e-10), Horner form in FP32.
+__device__ __forceinline__ void taylor_sin_cosm1(float d, float &sd, float &cm) {
+    constexpr float s3 = (float)(-1.0 / 6.0), s5 = (float)(1.0 / 120.0), s7 = (float)(-1.0 / 5040.0);
+    constexpr float s9 = (float)(1.0 / 362880.0), s11 = (float)(-1.0 / 39916800.0);
+    constexpr float c2 = -0.5f, c4 = (float)(1.0 / 24.0), c6 = (float)(-1.0 / 720.0), c8 = (float)(1.0 / 40320.0);
+    constexpr float c10 = (float)(-1.0 / 3628800.0), c12 = (float)(1.0 / 479001600.0);
+    const float d2 = __fmul_rn(d, d);
+    float p = fmaf(d2, s11, s9);
+    p = fmaf(d2, p, s7);
+    p = fmaf(d2, p, s5);
+    p = fmaf(d2, p, s3);
+    sd = fmaf(__fmul_rn(d, d2), p, d);
+    float c = fmaf(d2, c12, c10);
+    c = fmaf(d2, c, c8);
+    c = fmaf(d2, c, c6);
+    c = fmaf(d2, c, c4);
+    c = fmaf(d2, c, c2);
+    cm = __fmul_rn(d2, c);
+}
+
+// Point m = j - j_A (0 <= m < 32) of a ring relative to its anchor's cell: P - I.
+// (xa, ya): the anchor's local coordinates (hi parts); poly: the ring's flag (32 dphi <= 1).
+__device__ __forceinline__ float3 anchor_offset(const float f[3], float xa, float ya, const float ex[3],
+                                                const float ey[3], float dphi, float dphi_lo, int poly, int m) {
+    const float mf = __int2float_rn(m);
+    const float d = fmaf(mf, dphi_lo, __fmul_rn(mf, dphi));
+    float sd, cm;
+    if (poly) {
+        taylor_sin_cosm1(d, sd, cm);
+    } else {
+        float c;
+        sincosf(d, &sd, &c);
+        cm = __fsub_rn(c, 1.f);
+    }
+    const float dx = fmaf(-ya, sd, __fmul_rn(xa, cm));
+    const float dy = fmaf(xa, sd, __fmul_rn(ya, cm));
+    return make_float3(fmaf(dy, ey[0], fmaf(dx, ex[0], f[0])),
+                       fmaf(dy, ey[1], fmaf(dx, ex[1], f[1])),
+                       fmaf(dy, ey[2], fmaf(dx, ex[2], f[2])));
+}
+
+// Approximate ring centre B = O + h e_z in FP32 (azimuth windows only, which carry margins).
 __device__ __forceinline__ float3 ring_base(const float O[3], const float ez[3], float h) {
     return make_float3(fmaf(h, ez[0], O[0]), fmaf(h, ez[1], O[1]), fmaf(h, ez[2], O[2]));
 }
 
-// Lattice point P = B + u e_x + v e_y (index coordinates), fused multiply-adds in a fixed order.
-__device__ __forceinline__ float3 ring_point(float3 B, const float ex[3], const float ey[3], float u, float v) {
-    return make_float3(fmaf(v, ey[0], fmaf(u, ex[0], B.x)),
-                       fmaf(v, ey[1], fmaf(u, ex[1], B.y)),
-                       fmaf(v, ey[2], fmaf(u, ex[2], B.z)));
-}
-
 __device__ __forceinline__ float lerp1(float a, float b, float w) { return fmaf(w, b - a, a); }
-
-// sum_n alpha_n psi_n(P): trilinear interpolation with the nodes outside the grid absent
-// (Eq. expfunI).
-__device__ __forceinline__ float trilinear(const float *__restrict__ vol, int nx, int ny, int nz, float3 P) {
-    float fx = floorf(P.x), fy = floorf(P.y), fz = floorf(P.z);
-    int ix = (int)fx, iy = (int)fy, iz = (int)fz;
-    // all eight nodes outside (also rejects NaN: comparisons are false)
-    if (!(ix >= -1 && ix < nx && iy >= -1 && iy < ny && iz >= -1 && iz < nz)) return 0.f;
-    float wx = P.x - fx, wy = P.y - fy, wz = P.z - fz;
-    const int sy = nx, sz = nx * ny;
-    float v000, v001, v010, v011, v100, v101, v110, v111;
-    if (ix >= 0 && ix < nx - 1 && iy >= 0 && iy < ny - 1 && iz >= 0 && iz < nz - 1) {
-        const float *b = vol + (iz * ny + iy) * nx + ix;
-        v000 = __ldg(b);          v001 = __ldg(b + 1);
-        v010 = __ldg(b + sy);     v011 = __ldg(b + sy + 1);
-        v100 = __ldg(b + sz);     v101 = __ldg(b + sz + 1);
-        v110 = __ldg(b + sz + sy); v111 = __ldg(b + sz + sy + 1);
-    } else {
-        bool x0 = ix >= 0, x1 = ix + 1 < nx, y0 = iy >= 0, y1 = iy + 1 < ny, z0 = iz >= 0, z1 = iz + 1 < nz;
-        auto at = [&](bool ok, int x, int y, int z) -> float {
-            return ok ? __ldg(vol + (z * ny + y) * nx + x) : 0.f;
-        };
-        v000 = at(z0 && y0 && x0, ix, iy, iz);         v001 = at(z0 && y0 && x1, ix + 1, iy, iz);
-        v010 = at(z0 && y1 && x0, ix, iy + 1, iz);     v011 = at(z0 && y1 && x1, ix + 1, iy + 1, iz);
-        v100 = at(z1 && y0 && x0, ix, iy, iz + 1);     v101 = at(z1 && y0 && x1, ix + 1, iy, iz + 1);
-        v110 = at(z1 && y1 && x0, ix, iy + 1, iz + 1); v111 = at(z1 && y1 && x1, ix + 1, iy + 1, iz + 1);
-    }
-    float c00 = lerp1(v000, v001, wx), c01 = lerp1(v010, v011, wx);
-    float c10 = lerp1(v100, v101, wx), c11 = lerp1(v110, v111, wx);
-    float c0 = lerp1(c00, c01, wy), c1 = lerp1(c10, c11, wy);
-    return lerp1(c0, c1, wz);
-}
 
 // Neumaier compensated accumulation: (s, e) += x.
 __device__ __forceinline__ void kadd(float &s, float &e, float x) {

@@ -1,5 +1,5 @@
-// Host side of a plan: validation, the FP64 shell-lattice tables (Appendix), work items and
-// device upload.  Compiled without floating-point contraction so that the integer lattice
+// Host side of a plan: validation, the FP64 shell-lattice tables (Appendix), the brick tilings
+// and device upload.  Compiled without floating-point contraction so that the integer lattice
 // counts N_i and N_j come out of plain IEEE double arithmetic in the paper's formula order.
 #include <algorithm>
 #include <cmath>
@@ -14,7 +14,11 @@ namespace oat {
 
 namespace {
 
-constexpr int kTileQ = 8;   // transducers of one radius class per forward work item
+// v = hi + lo with hi = fl32(v) and lo = fl32(v - hi): a float pair carrying about 48 bits of v.
+void split(double v, float &hi, float &lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
 
 bool finite3(const double *v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
 
@@ -98,7 +102,7 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
     p->dt = 1.0 / g.fs_mhz;
     p->cd = g.gruneisen / (8.0 * M_PI * g.c_mm_per_us * g.c_mm_per_us * p->dt * p->dt);
     const double ds = g.spacing_mm;
-    for (int d = 0; d < 3; ++d) p->O[d] = (float)(-g.origin_mm[d] / ds);
+    for (int d = 0; d < 3; ++d) split(-g.origin_mm[d] / ds, p->O[d], p->O_lo[d]);
     p->ds2 = (float)(ds * ds);
     p->R0 = (float)(g.c_mm_per_us * g.t_min_us / ds);
     p->dR = (float)(g.c_mm_per_us * p->dt / ds);
@@ -116,7 +120,11 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
             return set_error(OAT_ERR_GEOMETRY, "oat_plan_create: transducer " + std::to_string(q) +
                                                    " is not outside the support sphere (|r_q| <= R)");
         }
-        for (int d = 0; d < 3; ++d) { xd[q].ex[d] = (float)ex[d]; xd[q].ey[d] = (float)ey[d]; xd[q].ez[d] = (float)ez[d]; }
+        for (int d = 0; d < 3; ++d) {
+            split(ex[d], xd[q].ex[d], xd[q].ex_lo[d]);
+            split(ey[d], xd[q].ey[d], xd[q].ey_lo[d]);
+            split(ez[d], xd[q].ez[d], xd[q].ez_lo[d]);
+        }
         xd[q].dist = (float)(rs[q] / ds);
         cls_of.emplace(rs[q], 0);
     }
@@ -125,9 +133,11 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
     p->n_cls = (int)cls_r.size();
     for (int q = 0; q < Q; ++q) xd[q].cls = cls_of[rs[q]];
 
-    // shell lattice per (class, k): rings i < N_i with N_j points each
+    // shell lattice per (class, k): rings i < N_i with N_j points each, and the anchors of every
+    // ring: points j = 32 t, local coordinates a (cos(j dphi), sin(j dphi)) as float pairs
     const int C = p->n_cls;
     std::vector<Ring> rings;
+    std::vector<float4> anchors;
     std::vector<int> ring_off((size_t)C * K), ring_cnt((size_t)C * K);
     p->cls_points.assign((size_t)C * K, 0);
     for (int c = 0; c < C; ++c) {
@@ -154,12 +164,27 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
                 double st = std::sin(th);
                 double dph = ds / (rho * st);
                 int nj = (int)std::floor(2.0 * M_PI / dph);
+                const double h = (rho * std::cos(th) - r_s) / ds, a = rho * st / ds;
                 Ring rr;
-                rr.h = (float)((rho * std::cos(th) - r_s) / ds);
-                rr.a = (float)(rho * st / ds);
-                rr.dphi = (float)dph;
+                split(h, rr.h, rr.h_lo);
+                rr.a = (float)a;
+                split(dph, rr.dphi, rr.dphi_lo);
                 rr.nj = nj;
-                if (nj == 0) { rr.dphi = 0.f; rr.a = 0.f; }
+                rr.poly = (32.0 * dph <= 1.0) ? 1 : 0;
+                rr.aoff = (int)anchors.size();
+                if (nj == 0) { rr.dphi = 0.f; rr.dphi_lo = 0.f; rr.a = 0.f; rr.poly = 1; }
+                const int na = (nj + kAnchorMask) >> kAnchorShift;
+                if (anchors.size() + (size_t)na >= (size_t)INT32_MAX) {
+                    delete p;
+                    return set_error(OAT_ERR_UNSUPPORTED, "oat_plan_create: lattice tables exceed 2^31 anchors");
+                }
+                for (int tt = 0; tt < na; ++tt) {
+                    const double phi = (double)(tt << kAnchorShift) * dph;
+                    float4 e;
+                    split(a * std::cos(phi), e.x, e.y);
+                    split(a * std::sin(phi), e.z, e.w);
+                    anchors.push_back(e);
+                }
                 rings.push_back(rr);
                 npts += nj;
             }
@@ -168,35 +193,16 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
         }
     }
     p->n_rings = (long long)rings.size();
+    p->n_anchors = (long long)anchors.size();
 
-    // transducers sorted by class; forward work items (class, k, tile) heaviest shells first
-    std::vector<int> qlist(Q);
-    for (int q = 0; q < Q; ++q) qlist[q] = q;
-    std::stable_sort(qlist.begin(), qlist.end(), [&](int a, int b) { return xd[a].cls < xd[b].cls; });
-    std::vector<int> cls_start(C + 1, 0), cls_n(C, 0);
+    std::vector<int> cls_n(C, 0);
     for (int q = 0; q < Q; ++q) cls_n[xd[q].cls]++;
-    for (int c = 0; c < C; ++c) cls_start[c + 1] = cls_start[c] + cls_n[c];
-    std::vector<int4> items;
     p->points_ball = 0;
     for (int c = 0; c < C; ++c)
-        for (int k = 0; k < K; ++k) {
-            long long np = p->cls_points[(size_t)c * K + k];
-            p->points_ball += np * cls_n[c];
-            if (np == 0) continue;
-            for (int s = 0; s < cls_n[c]; s += kTileQ)
-                items.push_back(make_int4(c, k, cls_start[c] + s, std::min(kTileQ, cls_n[c] - s)));
-        }
+        for (int k = 0; k < K; ++k) p->points_ball += p->cls_points[(size_t)c * K + k] * cls_n[c];
     if (p->points_ball == 0) {
         delete p;
         return set_error(OAT_ERR_GEOMETRY, "oat_plan_create: no shell of the time window meets the support sphere");
-    }
-    std::stable_sort(items.begin(), items.end(), [&](const int4 &a, const int4 &b) {
-        return p->cls_points[(size_t)a.x * K + a.y] > p->cls_points[(size_t)b.x * K + b.y];
-    });
-    p->n_items = (long long)items.size();
-    if (p->n_items >= (1LL << 31)) {
-        delete p;
-        return set_error(OAT_ERR_UNSUPPORTED, "oat_plan_create: too many work items");
     }
 
     p->max_shell_points = 0;
@@ -240,29 +246,6 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
         }
     }
 
-    // radial-lane work items: (class, block of 32 shells, tile of 8 transducers), heaviest first
-    std::vector<int4> ritems;
-    std::vector<long long> rwork;
-    for (int c = 0; c < C; ++c)
-        for (int kb = 0; kb < K; kb += 32) {
-            long long w = 0;
-            for (int k = kb; k < std::min(K, kb + 32); ++k) w += p->cls_points[(size_t)c * K + k];
-            if (w == 0) continue;
-            for (int s0 = 0; s0 < cls_n[c]; s0 += kTileQ) {
-                ritems.push_back(make_int4(c, kb, cls_start[c] + s0, std::min(kTileQ, cls_n[c] - s0)));
-                rwork.push_back(w);
-            }
-        }
-    {
-        std::vector<size_t> ord(ritems.size());
-        for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
-        std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) { return rwork[x] > rwork[y]; });
-        std::vector<int4> sorted(ritems.size());
-        for (size_t i = 0; i < ord.size(); ++i) sorted[i] = ritems[ord[i]];
-        ritems.swap(sorted);
-    }
-    p->n_ritems = (long long)ritems.size();
-
     std::vector<float> Rk(K), wD(K);
     std::vector<double> wD64(K);
     for (int k = 0; k < K; ++k) {
@@ -279,9 +262,9 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
     // one device blob for every table
     std::vector<unsigned char> blob;
     size_t o_rings = push_bytes(blob, rings), o_off = push_bytes(blob, ring_off), o_cnt = push_bytes(blob, ring_cnt);
-    size_t o_xd = push_bytes(blob, xd), o_ql = push_bytes(blob, qlist), o_it = push_bytes(blob, items);
+    size_t o_xd = push_bytes(blob, xd), o_an = push_bytes(blob, anchors);
     size_t o_rk = push_bytes(blob, Rk), o_wd = push_bytes(blob, wD), o_wd64 = push_bytes(blob, wD64);
-    size_t o_ri = push_bytes(blob, ritems);
+    std::vector<float4>().swap(anchors);
     p->table_bytes = (long long)blob.size();
 
     int prev = 0;
@@ -312,10 +295,6 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
     if ((e = cudaMalloc(&p->d_amax, 256)) != cudaSuccess) return fail(e, "cudaMalloc(scale scratch)");
     p->d_count = (unsigned long long *)((char *)p->d_amax + 128);
     p->scratch_bytes = (long long)(g_bytes + v_bytes + 256);
-    {
-        const char *env = std::getenv("OAT_FWD");
-        p->fwd_radial = !(env && std::string(env) == "brick");
-    }
     if (set_forward_attributes() != OAT_OK || set_adjoint_attributes() != OAT_OK) {
         std::string msg = std::string("oat_plan_create: ") + oat_last_error();
         fail(cudaSuccess, "kernel attributes");
@@ -328,12 +307,10 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
     p->t.ring_off = (const int *)(base + o_off);
     p->t.ring_cnt = (const int *)(base + o_cnt);
     p->t.xd = (const Xdcr *)(base + o_xd);
-    p->t.qlist = (const int *)(base + o_ql);
-    p->t.items = (const int4 *)(base + o_it);
+    p->t.anchors = (const float4 *)(base + o_an);
     p->t.Rk = (const float *)(base + o_rk);
     p->t.wD = (const float *)(base + o_wd);
     p->t.wD64 = (const double *)(base + o_wd64);
-    p->d_ritems = (const int4 *)(base + o_ri);
     *out = p;
     return OAT_OK;
 }
