@@ -72,19 +72,20 @@ __device__ __forceinline__ float gprime(const AdjArgs &a, int q, int k) {
 // accumulator and cleared.
 __device__ __forceinline__ void sadd(int *hi, unsigned int *lo, int idx, float x) {
     const int v = __float2int_rn(x);
-    if (v != 0) {
-        atomicAdd(hi + idx, v >> 15);
-        atomicAdd(lo + idx, (unsigned int)(v & 0x7fff));
-    }
+    atomicAdd(hi + idx, v >> 15);
+    atomicAdd(lo + idx, (unsigned int)(v & 0x7fff));
 }
 
 constexpr int kQueue = 64;   // per-warp queue of owned points (power of two, >= 63)
 
-// Scatter one owned point (cell-local weights wx, wy, wz; first node b) with value gq.
+// Scatter one owned point (cell-local weights wx, wy, wz; first node b in the low 16 bits of
+// e.w, the point's shell s within the unit above them) with value wg[s].
 template <int S1, int S2>
-__device__ __forceinline__ void scatter8(int *shi, unsigned int *slo, float4 e, float gq) {
+__device__ __forceinline__ void scatter8(int *shi, unsigned int *slo, float4 e, const float *wg) {
     const float wx = e.x, wy = e.y, wz = e.z;
-    const int b = __float_as_int(e.w);
+    const int bs = __float_as_int(e.w);
+    const int b = bs & 0xffff;
+    const float gq = wg[bs >> 16];
     const float ux = 1.f - wx, uy = 1.f - wy, uz = 1.f - wz;
     const float g00 = gq * uz * uy, g01 = gq * uz * wy, g10 = gq * wz * uy, g11 = gq * wz * wy;
     sadd(shi, slo, b, g00 * ux);           sadd(shi, slo, b + 1, g00 * wx);
@@ -115,26 +116,38 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
     __syncthreads();
 
     // bounding sphere and box of the brick's cells [L, L + E)
-    const float c[3] = {L[0] + 0.5f * E[0], L[1] + 0.5f * E[1], L[2] + 0.5f * E[2]};
-    const float blo[3] = {(float)L[0], (float)L[1], (float)L[2]};
-    const float bhi[3] = {(float)(L[0] + E[0]), (float)(L[1] + E[1]), (float)(L[2] + E[2])};
-    const float rb = 0.5f * sqrtf((float)(E[0] * E[0] + E[1] * E[1] + E[2] * E[2])) + 0.05f;
-    const float rb2 = rb * rb;
+    // brick centre c, cell box [blo, bhi) and bounding-sphere radius rb: block-shared constants
+    __shared__ float c[3], blo[3], bhi[3], rbs[2];
+    if (threadIdx.x < 3) {
+        const int d = threadIdx.x;
+        c[d] = L[d] + 0.5f * E[d];
+        blo[d] = (float)L[d];
+        bhi[d] = (float)(L[d] + E[d]);
+        if (d == 0) {
+            rbs[0] = 0.5f * sqrtf((float)(E[0] * E[0] + E[1] * E[1] + E[2] * E[2])) + 0.05f;
+            rbs[1] = rbs[0] * rbs[0];
+        }
+    }
+    __syncthreads();
+    const float &rb = rbs[0], &rb2 = rbs[1];
     // contributions |w g'| <= max|g'| map to at most 2^30 units
     const float scale = (float)pow2_scale((double)__uint_as_float(*a.amax) * (double)a.gscale, 30);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     SegSlot *ws = slots + warp * 32;
     float4 *wq = queues + warp * kQueue;
+    __shared__ float s_wg[kAdjThreads / 32][kShells];
+    float *wg = s_wg[warp];
     const unsigned lt_mask = (1u << lane) - 1u;
 
     for (int qp = q0; qp < q1; qp += a.qpass) {
         const int qe = min(q1, qp + a.qpass);
-        const int units = (qe - qp) * a.kspan;
+        const int nkg = (a.kspan + kShells - 1) / kShells;
+        const int units = (qe - qp) * nkg;
         int vq = -1;
         BrickView &v = views[warp];   // the current transducer's view of the brick (shared, per warp)
         float ex[3], ey[3];
         for (int u = warp; u < units; u += nwarps) {
-            const int q = qp + u / a.kspan;
+            const int q = qp + u / nkg;
             if (q != vq) {
                 __syncwarp();
                 if (lane == 0) brick_view(a.t.xd[q], a.O, c, rb, a.R0, a.dR, a.K, v);
@@ -143,32 +156,48 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
                 for (int d = 0; d < 3; ++d) { ex[d] = v.ex[d]; ey[d] = v.ey[d]; }
                 vq = q;
             }
-            const int k = v.k0 + u % a.kspan;
-            if (k > v.k1) continue;
-            const int ck = v.cls * a.K + k;
-            const int nr = __ldg(a.t.ring_cnt + ck);
-            int ilo, ihi;
-            if (!shell_ring_range(v, __ldg(a.t.Rk + k), nr, rb2, ilo, ihi)) continue;
-            const float gq = gprime<DT>(a, q, k) * scale;
-            if (gq == 0.f) continue;
-            const int off = __ldg(a.t.ring_off + ck);
+            const int kb = v.k0 + (u % nkg) * kShells;
+            if (kb > v.k1) continue;
+            // lanes 0..kShells-1: one shell each (skipped where g' is zero)
+            int n = 0, gbase = 0;
+            float gs = 0.f;
+            if (lane < kShells && kb + lane <= v.k1) {
+                const int k = kb + lane, ck = v.cls * a.K + k;
+                int ilo, ihi;
+                if (shell_ring_range(v, __ldg(a.t.Rk + k), __ldg(a.t.ring_cnt + ck), rb2, ilo, ihi)) {
+                    gs = gprime<DT>(a, q, k) * scale;
+                    if (gs != 0.f) {
+                        n = ihi - ilo + 1;
+                        gbase = __ldg(a.t.ring_off + ck) + ilo;
+                    }
+                }
+            }
+            int p0, p1, p2;
+            const int T = unit_shells(n, lane, p0, p1, p2);
+            if (T == 0) continue;
+            __syncwarp();
+            if (lane < kShells) wg[lane] = gs;   // g' of the unit's shells, read by scatter8
+            __syncwarp();
             int qh = 0, qt = 0;   // queue head and tail (warp-uniform)
-            for (int ib = ilo; ib <= ihi; ib += 32) {
+            for (int ib = 0; ib < T; ib += 32) {
+                int shell;
+                const int gidx = unit_ring(ib + lane, T, p0, p1, p2, gbase, shell);
                 int wa0, wna, wb0, wnb, sincl;
-                const int S = ring_windows(v, a.t.rings, off, ib, ihi, a.O, rb2, blo, bhi, lane, wa0, wna, wb0, wnb, sincl);
+                const int S = ring_windows(v, a.t.rings, gidx, a.O, rb2, blo, bhi, lane, wa0, wna, wb0, wnb, sincl);
                 for (int sc = 0; sc < S; sc += 32) {
                     int my_start;
-                    const int total = segment_chunk(a.t.xd + q, a.t.rings, a.t.anchors, off, ib, a.O, a.O_lo, L, sc, S,
-                                                    lane, wa0, wna, wb0, wnb, sincl, ws, my_start);
+                    const int total = segment_chunk(a.t.xd + q, a.t.rings, a.t.anchors, gidx, shell, a.O, a.O_lo, L,
+                                                    sc, S, lane, wa0, wna, wb0, wnb, sincl, ws, my_start);
                     for (int f = 0; f < total; f += 32) {
                         int lc[3];
                         float w[3];
                         bool own = false;
                         float4 ent;
-                        if (segment_point(ws, f, lane, my_start, total, ex, ey, lc, w)) {
+                        const int sh = segment_point(ws, f, lane, my_start, total, ex, ey, lc, w);
+                        if (sh >= 0) {
                             own = (unsigned)lc[0] < (unsigned)E[0] && (unsigned)lc[1] < (unsigned)E[1] &&
                                   (unsigned)lc[2] < (unsigned)E[2];
-                            ent = make_float4(w[0], w[1], w[2], __int_as_float(lc[2] * S2 + lc[1] * S1 + lc[0]));
+                            ent = make_float4(w[0], w[1], w[2], __int_as_float((lc[2] * S2 + lc[1] * S1 + lc[0]) | (sh << 16)));
                         }
                         // queue the owned points; scatter them 32 at a time with every lane busy
                         const unsigned om = __ballot_sync(0xffffffffu, own);
@@ -176,7 +205,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
                         qt += __popc(om);
                         __syncwarp();
                         if (qt - qh >= 32) {
-                            scatter8<S1, S2>(shi, slo, wq[(qh + lane) & (kQueue - 1)], gq);
+                            scatter8<S1, S2>(shi, slo, wq[(qh + lane) & (kQueue - 1)], wg);
                             qh += 32;
                             __syncwarp();
                         }
@@ -184,7 +213,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
                     __syncwarp();
                 }
             }
-            if (lane < qt - qh) scatter8<S1, S2>(shi, slo, wq[(qh + lane) & (kQueue - 1)], gq);
+            if (lane < qt - qh) scatter8<S1, S2>(shi, slo, wq[(qh + lane) & (kQueue - 1)], wg);
             __syncwarp();
         }
         __syncthreads();

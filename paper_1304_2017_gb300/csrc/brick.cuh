@@ -70,39 +70,28 @@ __device__ __forceinline__ bool shell_ring_range(const BrickView &v, float Rk, i
     return ilo <= ihi;
 }
 
-// Azimuth index ranges of ring r within rb of the centre: [a0, a1] and [b0, b1] (either may
-// be empty, i.e. lo > hi).  Returns false when the ring misses the sphere.
-__device__ __forceinline__ bool ring_ranges(const BrickView &v, const Ring &r, float rb2, int &a0, int &a1, int &b0,
-                                            int &b1) {
-    a0 = 0; a1 = -1; b0 = 0; b1 = -1;
-    if (r.nj == 0) return false;
-    const float dz = v.wz0 - r.h;
-    const float dr = v.rw - r.a;
-    const float rem = rb2 - dz * dz - dr * dr;
-    if (!(rem > 0.f)) return false;
-    const float den = 4.f * r.a * v.rw;
-    if (!(den > 1e-12f) || rem >= den) { a1 = r.nj - 1; return true; }
-    const float delta = 2.f * asinf(sqrtf(rem / den)) + 2e-3f;
-    if (delta >= 3.1f) { a1 = r.nj - 1; return true; }
-    const float inv = 1.f / r.dphi;
-    a0 = max(0, (int)ceilf((v.phc - delta) * inv));
-    a1 = min(r.nj - 1, (int)floorf((v.phc + delta) * inv));
-    if (v.phc - delta < 0.f) {          // window wraps below 0: points near 2 pi
-        b0 = max(0, (int)ceilf((v.phc - delta + kTwoPiF) * inv));
-        b1 = r.nj - 1;
-    } else if (v.phc + delta >= kTwoPiF) {   // wraps above 2 pi: points near 0
-        b0 = 0;
-        b1 = min(r.nj - 1, (int)floorf((v.phc + delta - kTwoPiF) * inv));
-    }
-    return true;
+// arccos(x), |x| <= 1, by Hastings' approximation (Abramowitz and Stegun, Handbook of
+// Mathematical Functions, 4.4.45): acos(x) ~ sqrt(1 - x) (a0 + a1 x + a2 x^2 + a3 x^3) on [0, 1]
+// and pi - acos(-x) below 0; absolute error below 7e-5 rad.  Used only for the azimuth windows,
+// whose 2e-3 rad margins cover it.
+__device__ __forceinline__ float acos_window(float x) {
+    const float ax = fminf(fabsf(x), 1.f);
+    float p = fmaf(ax, -0.0187293f, 0.0742610f);
+    p = fmaf(ax, p, -0.2121144f);
+    p = fmaf(ax, p, 1.5707288f);
+    const float t = fmaxf(1.f - ax, 1e-30f);
+    const float r = t * rsqrtf(t) * p;
+    return x < 0.f ? 3.14159265f - r : r;
 }
 
-// Azimuth index ranges of ring r (centre C) whose points can lie in the box lo <= P < hi:
-// the bounding-sphere window of ring_ranges, shrunk axis by axis to the hull of the azimuths at
+// Azimuth index ranges [a0, a1] and [b0, b1] (either may be empty, lo > hi; b holds the part
+// past 2 pi) of ring r (centre C) whose points can lie in the box lo <= P < hi: the window
+// |phi - phi_c| <= 2 asin(sqrt(rem / (4 a r_w))) in which the ring is within rb of the brick
+// centre (exact point-to-ring distance), shrunk axis by axis to the hull of the azimuths at
 // which the ring's coordinate d = C_d + a m_d cos(phi - psi_d) lies in [lo_d, hi_d] (two arcs
 // per axis from two arccosines; their hull inside the window keeps the window one interval).
-// Margins of 1e-3 grid units and 2e-3 rad keep it conservative; candidates are then tested
-// exactly with floor(P).
+// Margins of 1e-3 grid units and 2e-3 rad keep it conservative (the arccosines come from
+// acos_window); candidates are then tested exactly with their cells.
 __device__ __forceinline__ bool ring_box_ranges(const BrickView &v, const Ring &r, float3 C, float rb2,
                                                 const float lo[3], const float hi[3], int &a0, int &a1, int &b0,
                                                 int &b1) {
@@ -115,7 +104,7 @@ __device__ __forceinline__ bool ring_box_ranges(const BrickView &v, const Ring &
     const float den = 4.f * r.a * v.rw;
     float w0 = 0.f, w1 = kTwoPiF;
     if (den > 1e-12f && rem < den) {
-        const float delta = 2.f * asinf(sqrtf(rem / den)) + 2e-3f;
+        const float delta = acos_window(1.f - 2.f * (rem / den)) + 2e-3f;   // 2 asin(sqrt(rem / den))
         if (delta < 3.1f) { w0 = v.phc - delta; w1 = v.phc + delta; }
     }
     const float Cd[3] = {C.x, C.y, C.z};
@@ -131,8 +120,8 @@ __device__ __forceinline__ bool ring_box_ranges(const BrickView &v, const Ring &
         const float cl = (lo[d] - 1e-3f - Cd[d]) * inv, ch = (hi[d] + 1e-3f - Cd[d]) * inv;
         if (ch < -1.f || cl > 1.f) return false;
         if (cl <= -1.f && ch >= 1.f) continue;
-        const float ah = ch >= 1.f ? 0.f : acosf(ch);
-        const float al = cl <= -1.f ? kPi : acosf(cl);
+        const float ah = ch >= 1.f ? 0.f : acos_window(ch);
+        const float al = cl <= -1.f ? kPi : acos_window(cl);
         const float sh = kTwoPiF * floorf((w0 - v.psi[d] + kPi) * (1.f / kTwoPiF));
         const float x0 = w0 - v.psi[d] - sh, x1 = w1 - v.psi[d] - sh;   // x0 in [-pi, pi)
         float hl = 1e30f, hh = -1e30f;
@@ -162,11 +151,40 @@ __device__ __forceinline__ bool ring_box_ranges(const BrickView &v, const Ring &
 }
 
 // ---------------------------------------------------------------------------- candidates
-// A warp enumerates the candidates of one (transducer, shell) in three levels:
-//   rings     one lane per ring: its azimuth windows clipped to the brick (ring_windows);
+// A warp enumerates the candidates of one unit -- a transducer and kShells consecutive shells --
+// in three levels:
+//   rings     the units' rings, flattened over its shells, one lane per ring: the ring's azimuth
+//             windows clipped to the brick (ring_windows);
 //   segments  the part of a window that shares one anchor (j >> 5): up to 32 points.  One lane
 //             per segment computes the anchor and fills a slot (segment_chunk);
 //   points    the segments' points spread evenly over the lanes (segment_point).
+constexpr int kShells = 4;
+
+// Shells of a unit: lane s < kShells takes shell kb + s (if <= k1 and its rings can meet the
+// brick's bounding sphere): first ring gbase (in the ring table) and ring count n.  Returns the
+// unit's ring count; p0..p2 = inclusive prefixes of the ring counts of shells 0..2.
+// Warp-collective.
+__device__ __forceinline__ int unit_shells(int n, int lane, int &p0, int &p1, int &p2) {
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < kShells; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    p0 = __shfl_sync(0xffffffffu, incl, 0);
+    p1 = __shfl_sync(0xffffffffu, incl, 1);
+    p2 = __shfl_sync(0xffffffffu, incl, 2);
+    return __shfl_sync(0xffffffffu, incl, kShells - 1);
+}
+
+// Ring fi of a unit's flattened list: its shell s and its index in the ring table (-1 past the
+// end T).  gbase: lane s holds shell s's first ring.  Warp-collective.
+__device__ __forceinline__ int unit_ring(int fi, int T, int p0, int p1, int p2, int gbase, int &s) {
+    s = (fi >= p0) + (fi >= p1) + (fi >= p2);
+    const int before = s == 0 ? 0 : (s == 1 ? p0 : (s == 2 ? p1 : p2));
+    const int g = __shfl_sync(0xffffffffu, gbase, s) + (fi - before);
+    return fi < T ? g : -1;
+}
 
 // One anchor segment of a warp's chunk.
 struct SegSlot {
@@ -174,7 +192,7 @@ struct SegSlot {
     int I[3];            // anchor cell I, relative to the brick's lowest cell L
     float xa, ya;        // anchor local coordinates (hi parts)
     float dphi, dphi_lo;
-    int mp;              // m = j - j_A of the segment's first point | poly << 8
+    int mp;              // m = j - j_A of the segment's first point | poly << 8 | shell << 9
     int start;           // position of the segment's first point in the chunk's candidate list
 };
 
@@ -182,16 +200,15 @@ __device__ __forceinline__ int anchor_segments(int lo, int n) {
     return n > 0 ? ((lo + n - 1) >> kAnchorShift) - (lo >> kAnchorShift) + 1 : 0;
 }
 
-// Lane i - ib of rings ib..ihi of shell ck: the ring's windows [wa0, wa0 + wna) and
-// [wb0, wb0 + wnb) clipped to the brick, and the inclusive prefix over lanes of their anchor
-// segments.  Returns the batch's segment count.  Warp-collective.
-__device__ __forceinline__ int ring_windows(const BrickView &v, const Ring *__restrict__ rings, int off, int ib, int ihi,
+// Lane's ring gidx (none if < 0): its windows [wa0, wa0 + wna) and [wb0, wb0 + wnb) clipped to
+// the brick, and the inclusive prefix over lanes of their anchor segments.  Returns the batch's
+// segment count.  Warp-collective.
+__device__ __forceinline__ int ring_windows(const BrickView &v, const Ring *__restrict__ rings, int gidx,
                                             const float O[3], float rb2, const float blo[3], const float bhi[3],
                                             int lane, int &wa0, int &wna, int &wb0, int &wnb, int &sincl) {
-    const int i = ib + lane;
     int a0 = 0, a1 = -1, b0 = 0, b1 = -1;
-    if (i <= ihi) {
-        const Ring r = rings[off + i];
+    if (gidx >= 0) {
+        const Ring r = rings[gidx];
         ring_box_ranges(v, r, ring_base(O, v.ez, r.h), rb2, blo, bhi, a0, a1, b0, b1);
     }
     wa0 = a0; wna = max(0, a1 - a0 + 1);
@@ -210,9 +227,10 @@ __device__ __forceinline__ int ring_windows(const BrickView &v, const Ring *__re
 // chunk's number of candidates; my_start = first candidate of slot `lane` (INT_MAX if none).
 // Warp-collective.
 __device__ __forceinline__ int segment_chunk(const Xdcr *__restrict__ xq, const Ring *__restrict__ rings,
-                                             const float4 *__restrict__ anchors, int off, int ib, const float Oh[3],
-                                             const float Ol[3], const int L[3], int sc, int S, int lane, int wa0,
-                                             int wna, int wb0, int wnb, int sincl, SegSlot *ws, int &my_start) {
+                                             const float4 *__restrict__ anchors, int gidx, int shell,
+                                             const float Oh[3], const float Ol[3], const int L[3], int sc, int S,
+                                             int lane, int wa0, int wna, int wb0, int wnb, int sincl, SegSlot *ws,
+                                             int &my_start) {
     const int g = sc + lane;
     // owning ring lane: the number of lanes whose inclusive prefix is <= g
     int r = 0;
@@ -224,6 +242,7 @@ __device__ __forceinline__ int segment_chunk(const Xdcr *__restrict__ xq, const 
     const int ra0 = __shfl_sync(0xffffffffu, wa0, r), rna = __shfl_sync(0xffffffffu, wna, r);
     const int rb0 = __shfl_sync(0xffffffffu, wb0, r), rnb = __shfl_sync(0xffffffffu, wnb, r);
     const int rincl = __shfl_sync(0xffffffffu, sincl, r);
+    const int rg_idx = __shfl_sync(0xffffffffu, gidx, r), rshell = __shfl_sync(0xffffffffu, shell, r);
     int cnt = 0, j0 = 0, t = 0;
     if (g < S) {
         const int nsa = anchor_segments(ra0, rna), nsb = anchor_segments(rb0, rnb);
@@ -241,7 +260,7 @@ __device__ __forceinline__ int segment_chunk(const Xdcr *__restrict__ xq, const 
         if (lane >= o) incl += u;
     }
     if (cnt > 0) {
-        const Ring rg = rings[off + ib + r];
+        const Ring rg = rings[rg_idx];
         const float4 xy = __ldg(anchors + rg.aoff + t);
         int I[3];
         float fr[3];
@@ -251,7 +270,7 @@ __device__ __forceinline__ int segment_chunk(const Xdcr *__restrict__ xq, const 
         for (int d = 0; d < 3; ++d) { sl.f[d] = fr[d]; sl.I[d] = I[d] - L[d]; }
         sl.xa = xy.x; sl.ya = xy.z;
         sl.dphi = rg.dphi; sl.dphi_lo = rg.dphi_lo;
-        sl.mp = (j0 - (t << kAnchorShift)) | (rg.poly << 8);
+        sl.mp = (j0 - (t << kAnchorShift)) | (rg.poly << 8) | (rshell << 9);
         sl.start = incl - cnt;
     }
     my_start = cnt > 0 ? incl - cnt : 0x7fffffff;
@@ -259,25 +278,25 @@ __device__ __forceinline__ int segment_chunk(const Xdcr *__restrict__ xq, const 
     return __shfl_sync(0xffffffffu, incl, 31);
 }
 
-// Candidate f + lane of a chunk: its cell relative to the brick's lowest cell (lc) and its
-// position in that cell (w), through the shared lattice-point functions (ex, ey: the
-// transducer's frame, hi parts).  Warp-collective;
-// returns false for lanes past the end of the list.
-__device__ __forceinline__ bool segment_point(const SegSlot *ws, int f, int lane, int my_start, int total,
-                                              const float ex[3], const float ey[3], int lc[3], float w[3]) {
+// Candidate f + lane of a chunk: its cell relative to the brick's lowest cell (lc), its position
+// in that cell (w) and its shell within the unit (returned; -1 for lanes past the end of the
+// list), through the shared lattice-point functions (ex, ey: the transducer's frame, hi parts).
+// Warp-collective.
+__device__ __forceinline__ int segment_point(const SegSlot *ws, int f, int lane, int my_start, int total,
+                                             const float ex[3], const float ey[3], int lc[3], float w[3]) {
     const int before = __popc(__ballot_sync(0xffffffffu, my_start <= f));
     const unsigned inside =
         __reduce_or_sync(0xffffffffu, (my_start > f && my_start < f + 32) ? (1u << (my_start - f)) : 0u);
     const int cidx = f + lane;
-    if (cidx >= total) return false;
+    if (cidx >= total) return -1;
     const SegSlot &sl = ws[before - 1 + __popc(inside & ((2u << lane) - 1u))];
     const int mp = sl.mp;
-    const float3 R = anchor_offset(sl.f, sl.xa, sl.ya, ex, ey, sl.dphi, sl.dphi_lo, mp >> 8,
+    const float3 R = anchor_offset(sl.f, sl.xa, sl.ya, ex, ey, sl.dphi, sl.dphi_lo, (mp >> 8) & 1,
                                    (mp & 0xff) + (cidx - sl.start));
     const float fx = floorf(R.x), fy = floorf(R.y), fz = floorf(R.z);
     lc[0] = sl.I[0] + (int)fx; lc[1] = sl.I[1] + (int)fy; lc[2] = sl.I[2] + (int)fz;
     w[0] = __fsub_rn(R.x, fx); w[1] = __fsub_rn(R.y, fy); w[2] = __fsub_rn(R.z, fz);
-    return true;
+    return mp >> 9;
 }
 
 // Lowest cell L and cell counts E (<= bs) of brick id in a grid of nb[3] bricks (x fastest)

@@ -42,12 +42,14 @@ __device__ __forceinline__ void store_data(void *out, size_t i, float v) {
 // ---------------------------------------------------------------------------- bricks
 // k_brick_gather: one block per work item (brick of kBF^3 cells, range of transducers).  The
 // brick's (kBF+1)^3 nodes are staged in shared memory (zero outside the grid).  A warp takes one
-// (transducer, shell) unit at a time; one lane per ring computes the ring's azimuth window
-// clipped to the brick, one lane per anchor segment computes its anchor, the candidates are
-// spread evenly over the lanes (brick.cuh), and each point whose cell lies in the brick is
-// interpolated from shared memory.  The unit's
-// compensated FP32 sum is added to g[q][k] as a 64-bit fixed-point integer (one atomic per unit),
-// so the total does not depend on the order in which bricks finish.
+// unit (a transducer and kShells consecutive shells) at a time; one lane per ring computes the
+// ring's azimuth window clipped to the brick, one lane per anchor segment computes its anchor,
+// the candidates are spread evenly over the lanes (brick.cuh), and each point whose cell lies
+// in the brick is interpolated from shared memory.  A lane keeps a compensated FP32 sum of its
+// current shell's values and, when the shell changes, adds it as a 64-bit fixed-point integer to
+// its per-shell totals; the totals are summed over the warp and go to g[q][k] with one integer
+// atomic per shell and unit.  Integer addition makes the result independent of the order in
+// which lanes and bricks finish.
 constexpr int kFwdThreads = 1024;
 
 struct FwdArgs {
@@ -62,6 +64,11 @@ struct FwdArgs {
     float R0, dR;
     double bound_pts;             // max lattice points of one shell
 };
+
+// (s + e) rounded to the fixed-point unit 1 / scale.
+__device__ __forceinline__ long long to_fixed(float s, float e, double scale) {
+    return __double2ll_rn(((double)s + (double)e) * scale);
+}
 
 template <int B>
 __global__ void __launch_bounds__(kFwdThreads, 1) k_brick_gather(FwdArgs a) {
@@ -87,21 +94,31 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_brick_gather(FwdArgs a) {
     }
     __syncthreads();
 
-    const float c[3] = {L[0] + 0.5f * E[0], L[1] + 0.5f * E[1], L[2] + 0.5f * E[2]};
-    const float blo[3] = {(float)L[0], (float)L[1], (float)L[2]};
-    const float bhi[3] = {(float)(L[0] + E[0]), (float)(L[1] + E[1]), (float)(L[2] + E[2])};
-    const float rb = 0.5f * sqrtf((float)(E[0] * E[0] + E[1] * E[1] + E[2] * E[2])) + 0.05f;
-    const float rb2 = rb * rb;
+    // brick centre c, cell box [blo, bhi) and bounding-sphere radius rb: block-shared constants
+    __shared__ float c[3], blo[3], bhi[3], rbs[2];
+    if (threadIdx.x < 3) {
+        const int d = threadIdx.x;
+        c[d] = L[d] + 0.5f * E[d];
+        blo[d] = (float)L[d];
+        bhi[d] = (float)(L[d] + E[d]);
+        if (d == 0) {
+            rbs[0] = 0.5f * sqrtf((float)(E[0] * E[0] + E[1] * E[1] + E[2] * E[2])) + 0.05f;
+            rbs[1] = rbs[0] * rbs[0];
+        }
+    }
+    __syncthreads();
+    const float &rb = rbs[0], &rb2 = rbs[1];
     const double scale = pow2_scale(a.bound_pts * (double)__uint_as_float(*a.amax), 61);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     SegSlot *ws = slots + warp * 32;
-    const int units = (q1 - q0) * a.kspan;
+    const int nkg = (a.kspan + kShells - 1) / kShells;
+    const int units = (q1 - q0) * nkg;
     int vq = -1;
     BrickView &v = views[warp];   // the current transducer's view of the brick (shared, per warp)
     float ex[3], ey[3];
 
     for (int u = warp; u < units; u += nwarps) {
-        const int q = q0 + u / a.kspan;
+        const int q = q0 + u / nkg;
         if (q != vq) {
             __syncwarp();
             if (lane == 0) brick_view(a.t.xd[q], a.O, c, rb, a.R0, a.dR, a.K, v);
@@ -110,45 +127,71 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_brick_gather(FwdArgs a) {
             for (int d = 0; d < 3; ++d) { ex[d] = v.ex[d]; ey[d] = v.ey[d]; }
             vq = q;
         }
-        const int k = v.k0 + u % a.kspan;
-        if (k > v.k1) continue;
-        const int ck = v.cls * a.K + k;
-        const int nr = __ldg(a.t.ring_cnt + ck);
-        int ilo, ihi;
-        if (!shell_ring_range(v, __ldg(a.t.Rk + k), nr, rb2, ilo, ihi)) continue;
-        const int off = __ldg(a.t.ring_off + ck);
+        const int kb = v.k0 + (u % nkg) * kShells;
+        if (kb > v.k1) continue;
+        int n = 0, gbase = 0;
+        if (lane < kShells && kb + lane <= v.k1) {
+            const int k = kb + lane, ck = v.cls * a.K + k;
+            int ilo, ihi;
+            if (shell_ring_range(v, __ldg(a.t.Rk + k), __ldg(a.t.ring_cnt + ck), rb2, ilo, ihi)) {
+                n = ihi - ilo + 1;
+                gbase = __ldg(a.t.ring_off + ck) + ilo;
+            }
+        }
+        int p0, p1, p2;
+        const int T = unit_shells(n, lane, p0, p1, p2);
+        if (T == 0) continue;
+        // each lane sums its candidates of one shell at a time (candidates come in shell order)
+        // and, when the shell changes, moves the sum as a fixed-point integer into its per-shell
+        // totals t0..t3
         float acc = 0.f, err = 0.f;
-        for (int ib = ilo; ib <= ihi; ib += 32) {
+        int cur = 0;
+        long long t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+        for (int ib = 0; ib < T; ib += 32) {
+            int shell;
+            const int gidx = unit_ring(ib + lane, T, p0, p1, p2, gbase, shell);
             int wa0, wna, wb0, wnb, sincl;
-            const int S = ring_windows(v, a.t.rings, off, ib, ihi, a.O, rb2, blo, bhi, lane, wa0, wna, wb0, wnb, sincl);
+            const int S = ring_windows(v, a.t.rings, gidx, a.O, rb2, blo, bhi, lane, wa0, wna, wb0, wnb, sincl);
             for (int sc = 0; sc < S; sc += 32) {
                 int my_start;
-                const int total = segment_chunk(a.t.xd + q, a.t.rings, a.t.anchors, off, ib, a.O, a.O_lo, L, sc, S, lane,
-                                                wa0, wna, wb0, wnb, sincl, ws, my_start);
+                const int total = segment_chunk(a.t.xd + q, a.t.rings, a.t.anchors, gidx, shell, a.O, a.O_lo, L, sc, S,
+                                                lane, wa0, wna, wb0, wnb, sincl, ws, my_start);
                 for (int f = 0; f < total; f += 32) {
                     int lc[3];
                     float w[3];
-                    if (!segment_point(ws, f, lane, my_start, total, ex, ey, lc, w)) continue;
+                    const int sh = segment_point(ws, f, lane, my_start, total, ex, ey, lc, w);
+                    if (sh < 0) continue;
                     if ((unsigned)lc[0] < (unsigned)E[0] && (unsigned)lc[1] < (unsigned)E[1] && (unsigned)lc[2] < (unsigned)E[2]) {
                         const float *sp = sv + lc[2] * S2 + lc[1] * S1 + lc[0];
                         const float c00 = lerp1(sp[0], sp[1], w[0]), c01 = lerp1(sp[S1], sp[S1 + 1], w[0]);
                         const float c10 = lerp1(sp[S2], sp[S2 + 1], w[0]), c11 = lerp1(sp[S2 + S1], sp[S2 + S1 + 1], w[0]);
-                        kadd(acc, err, lerp1(lerp1(c00, c01, w[1]), lerp1(c10, c11, w[1]), w[2]));
+                        const float val = lerp1(lerp1(c00, c01, w[1]), lerp1(c10, c11, w[1]), w[2]);
+                        if (sh != cur) {
+                            const long long fx = to_fixed(acc, err, scale);
+                            if (cur == 0) t0 += fx; else if (cur == 1) t1 += fx; else if (cur == 2) t2 += fx; else t3 += fx;
+                            acc = 0.f; err = 0.f; cur = sh;
+                        }
+                        kadd(acc, err, val);
                     }
                 }
                 __syncwarp();
             }
         }
+        {
+            const long long fx = to_fixed(acc, err, scale);
+            if (cur == 0) t0 += fx; else if (cur == 1) t1 += fx; else if (cur == 2) t2 += fx; else t3 += fx;
+        }
+#pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const float s2 = __shfl_xor_sync(0xffffffffu, acc, o);
-            const float e2 = __shfl_xor_sync(0xffffffffu, err, o);
-            kadd(acc, err, s2);
-            err += e2;
+            t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+            t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+            t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+            t3 += __shfl_xor_sync(0xffffffffu, t3, o);
         }
-        if (lane == 0) {
-            const long long fxp = __double2ll_rn(((double)acc + (double)err) * scale);
-            if (fxp != 0) atomicAdd(a.gacc + (size_t)q * a.K + k, (unsigned long long)fxp);
-        }
+        // lane t < kShells adds shell t's total (integer addition: exact, order-independent)
+        const long long tot = lane == 0 ? t0 : (lane == 1 ? t1 : (lane == 2 ? t2 : t3));
+        if (lane < kShells && tot != 0 && kb + lane <= v.k1)
+            atomicAdd(a.gacc + (size_t)q * a.K + kb + lane, (unsigned long long)tot);
     }
 }
 
