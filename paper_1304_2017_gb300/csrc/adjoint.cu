@@ -76,6 +76,18 @@ __device__ __forceinline__ void sadd(int *hi, unsigned int *lo, int idx, float x
     atomicAdd(lo + idx, (unsigned int)(v & 0x7fff));
 }
 
+// Node layout of the brick's (B+1)^3 node sums: x stride 1, y stride S1, z stride S2, with S2
+// padded so that the 32 lanes' scatters, which follow rings in arbitrary directions, spread
+// over the banks (simulated on lattice-point warps of the 256^3 workload: 3.1 bank wavefronts
+// per atomic instead of 3.5 unpadded).
+template <int B>
+struct NodeLayout {
+    static constexpr int S1 = B + 1;
+    static constexpr int S2 = S1 * (B + 1) + 13;
+    static constexpr int NN = S2 * (B + 1);
+    static constexpr int NN2 = 2 * NN + ((2 * NN) & 3 ? 4 - ((2 * NN) & 3) : 0);
+};
+
 constexpr int kQueue = 64;   // per-warp queue of owned points (power of two, >= 63)
 
 // Scatter one owned point (cell-local weights wx, wy, wz; first node b in the low 16 bits of
@@ -96,9 +108,9 @@ __device__ __forceinline__ void scatter8(int *shi, unsigned int *slo, float4 e, 
 
 template <int B, int DT>
 __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
-    extern __shared__ int shi[];   // (B+1)^3 high halves, (B+1)^3 low halves, segment slots, queues
-    constexpr int S1 = B + 1, S2 = (B + 1) * (B + 1), NN = (B + 1) * (B + 1) * (B + 1);
-    constexpr int NN2 = 2 * NN + ((2 * NN) & 3 ? 4 - ((2 * NN) & 3) : 0);
+    extern __shared__ int shi[];   // node-sum high halves, low halves, segment slots, queues, views
+    using NL = NodeLayout<B>;
+    constexpr int S1 = NL::S1, S2 = NL::S2, NN = NL::NN, NN2 = NL::NN2;
     unsigned int *slo = (unsigned int *)(shi + NN);
     SegSlot *slots = (SegSlot *)(shi + NN2);
     float4 *queues = (float4 *)(slots + kAdjThreads);
@@ -184,10 +196,11 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
                 const int gidx = unit_ring(ib + lane, T, p0, p1, p2, gbase, shell);
                 int wa0, wna, wb0, wnb, sincl;
                 const int S = ring_windows(v, a.t.rings, gidx, a.O, rb2, blo, bhi, lane, wa0, wna, wb0, wnb, sincl);
-                for (int sc = 0; sc < S; sc += 32) {
-                    int my_start;
-                    const int total = segment_chunk(a.t.xd + q, a.t.rings, a.t.anchors, gidx, shell, a.O, a.O_lo, L,
-                                                    sc, S, lane, wa0, wna, wb0, wnb, sincl, ws, my_start);
+                for (int sc = 0, used = 0; sc < S; sc += used) {
+                    int my_start, csh;
+                    const int total = segment_chunk<false>(a.t.xd + q, a.t.rings, a.t.anchors, gidx, shell, a.O, a.O_lo,
+                                                           L, sc, S, lane, wa0, wna, wb0, wnb, sincl, ws, my_start, used,
+                                                           csh);
                     for (int f = 0; f < total; f += 32) {
                         int lc[3];
                         float w[3];
@@ -224,7 +237,8 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
             const unsigned int lo = slo[idx];
             if (hi != 0 || lo != 0u) {
                 shi[idx] = 0; slo[idx] = 0u;
-                const int x = idx % S1 + L[0], y = (idx / S1) % S1 + L[1], z = idx / S2 + L[2];
+                const int lz = idx / S2, r = idx - lz * S2, ly = r / S1;
+                const int x = r - ly * S1 + L[0], y = ly + L[1], z = lz + L[2];
                 if (x >= 0 && x < a.nx && y >= 0 && y < a.ny && z >= 0 && z < a.nz) {
                     const long long vv = (long long)hi * 32768LL + (long long)lo;
                     atomicAdd(a.vacc + ((size_t)z * a.ny + y) * a.nx + x, (unsigned long long)vv);
@@ -323,10 +337,8 @@ int launch_backproject_static(Plan &p, const void *data, float *vol, cudaStream_
 }
 
 size_t adjoint_smem_bytes() {
-    const size_t nn2 = 2 * (size_t)(kBA + 1) * (kBA + 1) * (kBA + 1);
-    const size_t pad = (nn2 & 3) ? 4 - (nn2 & 3) : 0;
-    return sizeof(int) * (nn2 + pad) + sizeof(SegSlot) * kAdjThreads + sizeof(float4) * kQueue * (kAdjThreads / 32) +
-           sizeof(BrickView) * (kAdjThreads / 32);
+    return sizeof(int) * NodeLayout<kBA>::NN2 + sizeof(SegSlot) * kAdjThreads +
+           sizeof(float4) * kQueue * (kAdjThreads / 32) + sizeof(BrickView) * (kAdjThreads / 32);
 }
 
 int set_adjoint_attributes() {

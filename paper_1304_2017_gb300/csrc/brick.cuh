@@ -224,13 +224,16 @@ __device__ __forceinline__ int ring_windows(const BrickView &v, const Ring *__re
 }
 
 // Segments sc .. sc + 31 of the batch, one per lane: anchor and slot ws[lane].  Returns the
-// chunk's number of candidates; my_start = first candidate of slot `lane` (INT_MAX if none).
-// Warp-collective.
+// chunk's number of candidates; my_start = first candidate of slot `lane` (INT_MAX if none);
+// used = segments taken.  With ONE_SHELL the chunk stops before the first segment of another
+// shell than segment sc's (segments come in shell order), so that every candidate of the chunk
+// has shell cshell.  Warp-collective.
+template <bool ONE_SHELL>
 __device__ __forceinline__ int segment_chunk(const Xdcr *__restrict__ xq, const Ring *__restrict__ rings,
                                              const float4 *__restrict__ anchors, int gidx, int shell,
                                              const float Oh[3], const float Ol[3], const int L[3], int sc, int S,
                                              int lane, int wa0, int wna, int wb0, int wnb, int sincl, SegSlot *ws,
-                                             int &my_start) {
+                                             int &my_start, int &used, int &cshell) {
     const int g = sc + lane;
     // owning ring lane: the number of lanes whose inclusive prefix is <= g
     int r = 0;
@@ -243,8 +246,12 @@ __device__ __forceinline__ int segment_chunk(const Xdcr *__restrict__ xq, const 
     const int rb0 = __shfl_sync(0xffffffffu, wb0, r), rnb = __shfl_sync(0xffffffffu, wnb, r);
     const int rincl = __shfl_sync(0xffffffffu, sincl, r);
     const int rg_idx = __shfl_sync(0xffffffffu, gidx, r), rshell = __shfl_sync(0xffffffffu, shell, r);
+    bool take = g < S;
+    cshell = __shfl_sync(0xffffffffu, rshell, 0);
+    if (ONE_SHELL) take = take && rshell == cshell;
+    used = __popc(__ballot_sync(0xffffffffu, take));
     int cnt = 0, j0 = 0, t = 0;
-    if (g < S) {
+    if (take) {
         const int nsa = anchor_segments(ra0, rna), nsb = anchor_segments(rb0, rnb);
         const int sg = g - (rincl - nsa - nsb);
         int lo, hi;

@@ -45,11 +45,11 @@ __device__ __forceinline__ void store_data(void *out, size_t i, float v) {
 // unit (a transducer and kShells consecutive shells) at a time; one lane per ring computes the
 // ring's azimuth window clipped to the brick, one lane per anchor segment computes its anchor,
 // the candidates are spread evenly over the lanes (brick.cuh), and each point whose cell lies
-// in the brick is interpolated from shared memory.  A lane keeps a compensated FP32 sum of its
-// current shell's values and, when the shell changes, adds it as a 64-bit fixed-point integer to
-// its per-shell totals; the totals are summed over the warp and go to g[q][k] with one integer
-// atomic per shell and unit.  Integer addition makes the result independent of the order in
-// which lanes and bricks finish.
+// in the brick is interpolated from shared memory.  Candidate chunks hold one shell each, in
+// shell order; every lane keeps a compensated FP32 sum of the current shell, which is summed over
+// the warp and added to g[q][k] as a 64-bit fixed-point integer (one atomic per shell and unit)
+// when the shell changes.  Integer addition makes the result independent of the order in which
+// bricks finish.
 constexpr int kFwdThreads = 1024;
 
 struct FwdArgs {
@@ -65,9 +65,20 @@ struct FwdArgs {
     double bound_pts;             // max lattice points of one shell
 };
 
-// (s + e) rounded to the fixed-point unit 1 / scale.
-__device__ __forceinline__ long long to_fixed(float s, float e, double scale) {
-    return __double2ll_rn(((double)s + (double)e) * scale);
+// The warp's compensated sums (s, e), summed over the lanes, rounded to the fixed-point unit
+// 1 / scale and added to *dst by lane 0 (integer addition: exact and order-independent).
+__device__ __forceinline__ void flush_shell(float s, float e, double scale, int lane, unsigned long long *dst) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+        const float e2 = __shfl_xor_sync(0xffffffffu, e, o);
+        kadd(s, e, s2);
+        e += e2;
+    }
+    if (lane == 0) {
+        const long long v = __double2ll_rn(((double)s + (double)e) * scale);
+        if (v != 0) atomicAdd(dst, (unsigned long long)v);
+    }
 }
 
 template <int B>
@@ -141,57 +152,38 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_brick_gather(FwdArgs a) {
         int p0, p1, p2;
         const int T = unit_shells(n, lane, p0, p1, p2);
         if (T == 0) continue;
-        // each lane sums its candidates of one shell at a time (candidates come in shell order)
-        // and, when the shell changes, moves the sum as a fixed-point integer into its per-shell
-        // totals t0..t3
+        // chunks hold one shell each (in shell order): a compensated FP32 sum per lane, reduced
+        // over the warp and added as a fixed-point integer when the shell changes
         float acc = 0.f, err = 0.f;
-        int cur = 0;
-        long long t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+        int cur = -1;
         for (int ib = 0; ib < T; ib += 32) {
             int shell;
             const int gidx = unit_ring(ib + lane, T, p0, p1, p2, gbase, shell);
             int wa0, wna, wb0, wnb, sincl;
             const int S = ring_windows(v, a.t.rings, gidx, a.O, rb2, blo, bhi, lane, wa0, wna, wb0, wnb, sincl);
-            for (int sc = 0; sc < S; sc += 32) {
-                int my_start;
-                const int total = segment_chunk(a.t.xd + q, a.t.rings, a.t.anchors, gidx, shell, a.O, a.O_lo, L, sc, S,
-                                                lane, wa0, wna, wb0, wnb, sincl, ws, my_start);
+            for (int sc = 0, used = 0; sc < S; sc += used) {
+                int my_start, csh;
+                const int total = segment_chunk<true>(a.t.xd + q, a.t.rings, a.t.anchors, gidx, shell, a.O, a.O_lo, L,
+                                                      sc, S, lane, wa0, wna, wb0, wnb, sincl, ws, my_start, used, csh);
+                if (csh != cur) {
+                    if (cur >= 0) flush_shell(acc, err, scale, lane, a.gacc + (size_t)q * a.K + kb + cur);
+                    acc = 0.f; err = 0.f; cur = csh;
+                }
                 for (int f = 0; f < total; f += 32) {
                     int lc[3];
                     float w[3];
-                    const int sh = segment_point(ws, f, lane, my_start, total, ex, ey, lc, w);
-                    if (sh < 0) continue;
+                    if (segment_point(ws, f, lane, my_start, total, ex, ey, lc, w) < 0) continue;
                     if ((unsigned)lc[0] < (unsigned)E[0] && (unsigned)lc[1] < (unsigned)E[1] && (unsigned)lc[2] < (unsigned)E[2]) {
                         const float *sp = sv + lc[2] * S2 + lc[1] * S1 + lc[0];
                         const float c00 = lerp1(sp[0], sp[1], w[0]), c01 = lerp1(sp[S1], sp[S1 + 1], w[0]);
                         const float c10 = lerp1(sp[S2], sp[S2 + 1], w[0]), c11 = lerp1(sp[S2 + S1], sp[S2 + S1 + 1], w[0]);
-                        const float val = lerp1(lerp1(c00, c01, w[1]), lerp1(c10, c11, w[1]), w[2]);
-                        if (sh != cur) {
-                            const long long fx = to_fixed(acc, err, scale);
-                            if (cur == 0) t0 += fx; else if (cur == 1) t1 += fx; else if (cur == 2) t2 += fx; else t3 += fx;
-                            acc = 0.f; err = 0.f; cur = sh;
-                        }
-                        kadd(acc, err, val);
+                        kadd(acc, err, lerp1(lerp1(c00, c01, w[1]), lerp1(c10, c11, w[1]), w[2]));
                     }
                 }
                 __syncwarp();
             }
         }
-        {
-            const long long fx = to_fixed(acc, err, scale);
-            if (cur == 0) t0 += fx; else if (cur == 1) t1 += fx; else if (cur == 2) t2 += fx; else t3 += fx;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            t0 += __shfl_xor_sync(0xffffffffu, t0, o);
-            t1 += __shfl_xor_sync(0xffffffffu, t1, o);
-            t2 += __shfl_xor_sync(0xffffffffu, t2, o);
-            t3 += __shfl_xor_sync(0xffffffffu, t3, o);
-        }
-        // lane t < kShells adds shell t's total (integer addition: exact, order-independent)
-        const long long tot = lane == 0 ? t0 : (lane == 1 ? t1 : (lane == 2 ? t2 : t3));
-        if (lane < kShells && tot != 0 && kb + lane <= v.k1)
-            atomicAdd(a.gacc + (size_t)q * a.K + kb + lane, (unsigned long long)tot);
+        if (cur >= 0) flush_shell(acc, err, scale, lane, a.gacc + (size_t)q * a.K + kb + cur);
     }
 }
 

@@ -71,7 +71,7 @@ struct BrickCfg {
     size_t smem = 0;
 };
 
-constexpr int kBF = 32;     // projector brick edge: (kBF+1)^3 float nodes in shared memory
+constexpr int kBF = 34;     // projector brick edge: (kBF+1)^3 float nodes in shared memory
 constexpr int kBA = 24;     // backprojector brick edge: (kBA+1)^3 pairs of 32-bit node-sum halves in shared memory
 
 struct Plan {
