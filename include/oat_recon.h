@@ -30,9 +30,12 @@ extern "C" {
  *   r = (1 + beta) hx - beta hx_prev - u        (= H y_{k+1} - u by linearity of H)
  *   acc[0] += sum (hx - u)^2,  acc[1] += sum u^2   (double; caller zeroes acc)
  * hx_prev may equal hx (beta ignored then).  r may alias hx_prev.  n elements.
+ * The measured data u are stored as u_dtype (OAT_F32, OAT_F16 or OAT_BF16, oat.h) and read
+ * exactly; everything else is float32.  Returns OAT_ERR_INVALID_ARG for a bad size, dtype or
+ * pointer (float pointers must be 16-byte aligned).
  */
-int oat_fista_residual(long long n, const float *hx, const float *hx_prev, const float *u, float beta, float *r,
-                       double *acc, void *stream);
+int oat_fista_residual(long long n, const float *hx, const float *hx_prev, const void *u, int u_dtype, float beta,
+                       float *r, double *acc, void *stream);
 
 /*
  * Proximal map of lam * TV plus the constraint x >= 0 at z - step * g (the FISTA gradient

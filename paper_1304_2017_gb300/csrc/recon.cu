@@ -11,6 +11,9 @@
 #include <cmath>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "../../include/oat_recon.h"
 #include "oat_internal.h"
 
@@ -30,12 +33,20 @@ __device__ __forceinline__ void block_add(double v, double *out) {
     }
 }
 
+template <int DT>
+__device__ __forceinline__ float load_u(const void *u, long long i) {
+    if (DT == OAT_F32) return ((const float *)u)[i];
+    if (DT == OAT_F16) return __half2float(((const __half *)u)[i]);
+    return __bfloat162float(((const __nv_bfloat16 *)u)[i]);
+}
+
+template <int DT>
 __global__ void __launch_bounds__(kRThreads) k_fista_residual(long long n, const float *__restrict__ hx,
-                                                              const float *__restrict__ hp, const float *__restrict__ u,
+                                                              const float *__restrict__ hp, const void *__restrict__ u,
                                                               float beta, float *r, double *acc) {
     double s0 = 0.0, s1 = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const float h = hx[i], uu = u[i];
+        const float h = hx[i], uu = load_u<DT>(u, i);
         const float prev = hp[i];
         const double d = (double)h - (double)uu;
         s0 += d * d;
@@ -130,12 +141,16 @@ using namespace oat;
 
 extern "C" {
 
-int oat_fista_residual(long long n, const float *hx, const float *hx_prev, const float *u, float beta, float *r,
-                       double *acc, void *stream) {
-    if (n < 0 || !hx || !hx_prev || !u || !r || !acc || !al16(hx) || !al16(hx_prev) || !al16(u) || !al16(r))
-        return set_error(OAT_ERR_INVALID_ARG, "oat_fista_residual: bad size or pointer");
+int oat_fista_residual(long long n, const float *hx, const float *hx_prev, const void *u, int u_dtype, float beta,
+                       float *r, double *acc, void *stream) {
+    if (n < 0 || !hx || !hx_prev || !u || !r || !acc || !al16(hx) || !al16(hx_prev) || !al16(u) || !al16(r) ||
+        (u_dtype != OAT_F32 && u_dtype != OAT_F16 && u_dtype != OAT_BF16))
+        return set_error(OAT_ERR_INVALID_ARG, "oat_fista_residual: bad size, dtype or pointer");
     if (n == 0) return OAT_OK;
-    k_fista_residual<<<grid_for(n), kRThreads, 0, (cudaStream_t)stream>>>(n, hx, hx_prev, u, beta, r, acc);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (u_dtype == OAT_F32) k_fista_residual<OAT_F32><<<grid_for(n), kRThreads, 0, s>>>(n, hx, hx_prev, u, beta, r, acc);
+    else if (u_dtype == OAT_F16) k_fista_residual<OAT_F16><<<grid_for(n), kRThreads, 0, s>>>(n, hx, hx_prev, u, beta, r, acc);
+    else k_fista_residual<OAT_BF16><<<grid_for(n), kRThreads, 0, s>>>(n, hx, hx_prev, u, beta, r, acc);
     return check_launch("oat_fista_residual");
 }
 

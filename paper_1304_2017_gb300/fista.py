@@ -65,8 +65,10 @@ class FistaTV:
         return self.L
 
     def solve(self, u, iters, tol=None, x0=None, callback=None):
-        """Run up to `iters` iterations from x0 (zeros if None).  Returns (x, info) with the
-        relative data residuals of the iterates and the cumulative GPU time (CUDA events)."""
+        """Run up to `iters` iterations from x0 (zeros if None).  u: the measured data, float32,
+        float16 or bfloat16 (read exactly; the iteration itself runs in float32 on a float32
+        plan).  Returns (x, info) with the relative data residuals of the iterates and the
+        cumulative GPU time (CUDA events)."""
         if self.L is None:
             self.lipschitz()
         plan, s = self.plan, self._s()
@@ -82,7 +84,8 @@ class FistaTV:
         ev0.record()
         plan.project(self.x_prev, out=self.hx_prev)
         self.acc.zero_()
-        oat.oat_fista_residual(self.M, self.hx_prev.data_ptr(), self.hx_prev.data_ptr(), u.data_ptr(), 0.0,
+        ud = oat.dtype_code(u.dtype)
+        oat.oat_fista_residual(self.M, self.hx_prev.data_ptr(), self.hx_prev.data_ptr(), u.data_ptr(), ud, 0.0,
                                self.r.data_ptr(), self.acc.data_ptr(), s)
         res0 = math.sqrt(float(self.acc[0]) / max(float(self.acc[1]), 1e-300))
         t = 1.0
@@ -95,7 +98,7 @@ class FistaTV:
             tn = 0.5 * (1.0 + math.sqrt(1.0 + 4.0 * t * t))
             beta = (t - 1.0) / tn
             self.acc.zero_()
-            oat.oat_fista_residual(self.M, self.hx.data_ptr(), self.hx_prev.data_ptr(), u.data_ptr(), beta,
+            oat.oat_fista_residual(self.M, self.hx.data_ptr(), self.hx_prev.data_ptr(), u.data_ptr(), ud, beta,
                                    self.r.data_ptr(), self.acc.data_ptr(), s)     # r = H y_{k+1} - u
             oat.oat_fista_momentum(self.N, self.x.data_ptr(), self.x_prev.data_ptr(), beta, self.y.data_ptr(), s)
             self.x, self.x_prev = self.x_prev, self.x

@@ -61,7 +61,7 @@ def _load():
     lib.oat_plan_kernel_time.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_longlong)]
     ll, f32, i32 = ctypes.c_longlong, ctypes.c_float, ctypes.c_int
-    lib.oat_fista_residual.argtypes = [ll, vp, vp, vp, f32, vp, vp, vp]
+    lib.oat_fista_residual.argtypes = [ll, vp, vp, vp, i32, f32, vp, vp, vp]
     lib.oat_tv_prox.argtypes = [i32, i32, i32, vp, vp, f32, f32, i32, vp, vp, vp]
     lib.oat_fista_momentum.argtypes = [ll, vp, vp, f32, vp, vp]
     lib.oat_dot.argtypes = [ll, vp, vp, vp, vp]
@@ -151,8 +151,8 @@ def _p(x):
     return ctypes.c_void_p(x)
 
 
-def oat_fista_residual(n, hx, hx_prev, u, beta, r, acc, stream=0):
-    return _check(lib.oat_fista_residual(n, _p(hx), _p(hx_prev), _p(u), beta, _p(r), _p(acc), _p(stream)))
+def oat_fista_residual(n, hx, hx_prev, u, u_dtype, beta, r, acc, stream=0):
+    return _check(lib.oat_fista_residual(n, _p(hx), _p(hx_prev), _p(u), u_dtype, beta, _p(r), _p(acc), _p(stream)))
 
 
 def oat_tv_prox(nx, ny, nz, z, g, step, lam, iters, out, work, stream=0):
@@ -175,6 +175,15 @@ def oat_tv_value(nx, ny, nz, x, acc, stream=0):
 # ---- torch wrapper ---------------------------------------------------------------------
 
 _DT = {OAT_F32: "float32", OAT_F16: "float16", OAT_BF16: "bfloat16"}
+
+
+def dtype_code(torch_dtype):
+    """OAT_F32 / OAT_F16 / OAT_BF16 for a torch dtype (ValueError otherwise)."""
+    name = str(torch_dtype).replace("torch.", "")
+    for code, n in _DT.items():
+        if n == name:
+            return code
+    raise ValueError(f"unsupported data dtype {torch_dtype}")
 
 
 class Plan:

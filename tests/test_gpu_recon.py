@@ -55,7 +55,8 @@ def test_vector_kernels(env):
     acc = torch.zeros(4, dtype=torch.float64, device="cuda")
     r = torch.empty_like(ta)
     s = torch.cuda.current_stream().cuda_stream
-    oat.oat_fista_residual(n, ta.data_ptr(), tb.data_ptr(), tc.data_ptr(), 0.37, r.data_ptr(), acc.data_ptr(), s)
+    oat.oat_fista_residual(n, ta.data_ptr(), tb.data_ptr(), tc.data_ptr(), oat.OAT_F32, 0.37, r.data_ptr(),
+                           acc.data_ptr(), s)
     torch.cuda.synchronize()
     a64, b64, c64 = (v.astype(np.float64) for v in (a, b, c))
     assert rel(r.cpu().numpy(), 1.37 * a64 - 0.37 * b64 - c64) <= 1e-6
@@ -92,6 +93,32 @@ def test_fista_matches_reference(env):
     assert rel(x.cpu().numpy(), xr) <= 1e-4
     assert np.allclose(info["residual"], res_ref, rtol=1e-4)
     assert res_ref[-1] < res_ref[0]
+    plan.close()
+
+
+@pytest.mark.parametrize("name,unit", [("float32", 2.0 ** -24), ("float16", 2.0 ** -11), ("bfloat16", 2.0 ** -8)])
+def test_fista_data_storage_against_reference(env, name, unit):
+    """Measured data (3% Gaussian noise) stored as float32 / float16 / bfloat16, FP32 iteration
+    with FP64 reductions: the final iterate against the FP64 reference run on the unrounded data.
+    The difference is the storage rounding carried through (bounded here by 4 units of the
+    format, plus the FP32 parity tolerance)."""
+    torch, oat = env
+    from paper_1304_2017_gb300.fista import FistaTV
+    geom = W.make_geometry(16, 0.3, 3, 4, 7.0, 64)
+    truth = W.spheres_phantom(geom, 3, seed=12)
+    u = oracle.H(geom, truth)
+    rng = np.random.default_rng(14)
+    u = u + 0.03 * np.abs(u).max() * rng.standard_normal(u.shape)
+    plan = oat.Plan(geom)
+    solver = FistaTV(plan, mu=2e-3, inner=8)
+    L = solver.lipschitz(iters=40)
+    ut = torch.from_numpy(u.astype(np.float32)).cuda().to(getattr(torch, name))
+    x, _ = solver.solve(ut, iters=6)
+    xr, _ = recon.fista_tv(lambda v: oracle.H(geom, v), lambda v: oracle.Ht(geom, v), u, 2e-3, L, 6,
+                           np.zeros(geom.vol_shape), inner=8)
+    err = rel(x.cpu().numpy(), xr)
+    print(name, "final reconstruction: rel L2 vs FP64 reference", err)
+    assert err <= 4 * unit + 1e-4
     plan.close()
 
 
