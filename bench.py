@@ -109,6 +109,19 @@ def _dist():
     return world, rank, local
 
 
+def replica_throughput(ms, pts, world, device):
+    """Whole-job interp-samples/s of `world` replicas that each ran one H + one H^T of `pts`
+    samples per step in `ms` milliseconds: the slowest replica's time counts (max over ranks).
+    Returns (value, ms_max)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return world * 2.0 * pts / (ms_max * 1e-3), ms_max
+
+
 def cpu_baseline(geom, alpha, y, n_xdcr=32, points_per_xdcr=None):
     """Time the FP64 oracle (as it stands) for H and H^T on a transducer subset of the workload."""
     import oracle
@@ -269,11 +282,7 @@ def main():
     plan.set_profiling(False)
     g_ms, g_n = plan.kernel_time(0, reset=True)
     b_ms, b_n = plan.kernel_time(1, reset=True)
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * 2.0 * pts / (ms_max * 1e-3)
+    value, ms_max = replica_throughput(ms, pts, world, dev)
 
     # end to end through the public API with host buffers: pinned H2D of alpha and y, H and
     # H^T, D2H of u and alpha'
@@ -297,10 +306,7 @@ def main():
     e1.record(stream)
     barrier()
     e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
-    t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * 2.0 * pts / (float(t.item()) * 1e-3)
+    e2e_value, _ = replica_throughput(e2e_ms, pts, world, dev)
     bi = h_alpha.numel() * 4 + h_y.numel() * 4
     bo = h_u.numel() * 4 + h_a.numel() * 4
 

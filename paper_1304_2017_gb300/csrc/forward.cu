@@ -6,7 +6,7 @@
 //                  neighbouring samples cancels by one to three digits -- with one rounding to
 //                  float32 / float16 / bfloat16 at the end.
 // k_absmax         max |x| of a buffer (the fixed-point units of both directions).
-// k_count          lattice points whose stencil touches the grid (oat_plan_query).
+// k_brick_gather<COUNT>  lattice points whose stencil touches the grid (oat_plan_query).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -63,6 +63,7 @@ struct FwdArgs {
     float O[3], O_lo[3];
     float R0, dR;
     double bound_pts;             // max lattice points of one shell
+    unsigned long long *count;    // COUNT mode: owned lattice points
 };
 
 // The warp's compensated sums (s, e), summed over the lanes, rounded to the fixed-point unit
@@ -81,7 +82,9 @@ __device__ __forceinline__ void flush_shell(float s, float e, double scale, int 
     }
 }
 
-template <int B>
+// COUNT: instead of interpolating, count the points each brick owns (the bricks tile the cells
+// [-1, n-1]^3, so the total is the number of lattice points whose stencil touches the grid).
+template <int B, bool COUNT>
 __global__ void __launch_bounds__(kFwdThreads, 1) k_brick_gather(FwdArgs a) {
     extern __shared__ float sv[];   // (B+1)^3 nodes of the brick, then the warps' segment slots
     constexpr int S1 = B + 1, S2 = (B + 1) * (B + 1), NN = (B + 1) * (B + 1) * (B + 1);
@@ -97,7 +100,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_brick_gather(FwdArgs a) {
         const int n[3] = {a.nx, a.ny, a.nz};
         brick_box(brick, a.nb, a.bs, n, L, E);
     }
-    for (int idx = threadIdx.x; idx < NN; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < (COUNT ? 0 : NN); idx += blockDim.x) {
         const int x = idx % S1 + L[0], y = (idx / S1) % S1 + L[1], z = idx / S2 + L[2];
         float val = 0.f;
         if (x >= 0 && x < a.nx && y >= 0 && y < a.ny && z >= 0 && z < a.nz) val = __ldg(a.vol + ((size_t)z * a.ny + y) * a.nx + x);
@@ -119,8 +122,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_brick_gather(FwdArgs a) {
     }
     __syncthreads();
     const float &rb = rbs[0], &rb2 = rbs[1];
-    const double scale = pow2_scale(a.bound_pts * (double)__uint_as_float(*a.amax), 61);
+    const double scale = COUNT ? 1.0 : pow2_scale(a.bound_pts * (double)__uint_as_float(*a.amax), 61);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    unsigned long long owned = 0;   // COUNT mode
     SegSlot *ws = slots + warp * 32;
     const int nkg = (a.kspan + kShells - 1) / kShells;
     const int units = (q1 - q0) * nkg;
@@ -166,7 +170,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_brick_gather(FwdArgs a) {
                 const int total = segment_chunk<true>(a.t.xd + q, a.t.rings, a.t.anchors, gidx, shell, a.O, a.O_lo, L,
                                                       sc, S, lane, wa0, wna, wb0, wnb, sincl, ws, my_start, used, csh);
                 if (csh != cur) {
-                    if (cur >= 0) flush_shell(acc, err, scale, lane, a.gacc + (size_t)q * a.K + kb + cur);
+                    if (!COUNT && cur >= 0) flush_shell(acc, err, scale, lane, a.gacc + (size_t)q * a.K + kb + cur);
                     acc = 0.f; err = 0.f; cur = csh;
                 }
                 for (int f = 0; f < total; f += 32) {
@@ -174,6 +178,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_brick_gather(FwdArgs a) {
                     float w[3];
                     if (segment_point(ws, f, lane, my_start, total, ex, ey, lc, w) < 0) continue;
                     if ((unsigned)lc[0] < (unsigned)E[0] && (unsigned)lc[1] < (unsigned)E[1] && (unsigned)lc[2] < (unsigned)E[2]) {
+                        if (COUNT) { ++owned; continue; }
                         const float *sp = sv + lc[2] * S2 + lc[1] * S1 + lc[0];
                         const float c00 = lerp1(sp[0], sp[1], w[0]), c01 = lerp1(sp[S1], sp[S1 + 1], w[0]);
                         const float c10 = lerp1(sp[S2], sp[S2 + 1], w[0]), c11 = lerp1(sp[S2 + S1], sp[S2 + S1 + 1], w[0]);
@@ -183,7 +188,12 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_brick_gather(FwdArgs a) {
                 __syncwarp();
             }
         }
-        if (cur >= 0) flush_shell(acc, err, scale, lane, a.gacc + (size_t)q * a.K + kb + cur);
+        if (!COUNT && cur >= 0) flush_shell(acc, err, scale, lane, a.gacc + (size_t)q * a.K + kb + cur);
+    }
+    if (COUNT) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) owned += __shfl_xor_sync(0xffffffffu, owned, o);
+        if (lane == 0 && owned) atomicAdd(a.count, owned);
     }
 }
 
@@ -210,9 +220,24 @@ size_t forward_smem_bytes() {
 }
 
 int set_forward_attributes() {
-    cudaError_t e = cudaFuncSetAttribute(k_brick_gather<kBF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_brick_gather<kBF, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)forward_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_brick_gather<kBF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)forward_smem_bytes());
     return e == cudaSuccess ? OAT_OK : set_error(OAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+}
+
+static void fill_forward_args(const Plan &p, const float *vol, FwdArgs &a) {
+    a.t = p.t; a.vol = vol;
+    a.gacc = (unsigned long long *)p.d_gacc;
+    a.amax = p.d_amax;
+    a.nx = p.nx; a.ny = p.ny; a.nz = p.nz; a.K = p.K; a.Q = p.Q;
+    for (int d = 0; d < 3; ++d) { a.nb[d] = p.fwd.nb[d]; a.bs[d] = p.fwd.bs[d]; a.O[d] = p.O[d]; a.O_lo[d] = p.O_lo[d]; }
+    a.qchunk = p.fwd.qchunk; a.kspan = p.fwd.kspan;
+    a.R0 = p.R0; a.dR = p.dR;
+    a.bound_pts = (double)p.max_shell_points;
+    a.count = nullptr;
 }
 
 int launch_project(Plan &p, const float *vol, void *data, cudaStream_t s) {
@@ -222,17 +247,10 @@ int launch_project(Plan &p, const float *vol, void *data, cudaStream_t s) {
     if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_project: memset: ") + cudaGetErrorString(e));
     k_absmax<<<(unsigned)std::min<size_t>((N + 255) / 256, 152 * 8), 256, 0, s>>>(vol, N, OAT_F32, p.d_amax);
     FwdArgs a;
-    a.t = p.t; a.vol = vol;
-    a.gacc = (unsigned long long *)p.d_gacc;
-    a.amax = p.d_amax;
-    a.nx = p.nx; a.ny = p.ny; a.nz = p.nz; a.K = p.K; a.Q = p.Q;
-    for (int d = 0; d < 3; ++d) { a.nb[d] = p.fwd.nb[d]; a.bs[d] = p.fwd.bs[d]; a.O[d] = p.O[d]; a.O_lo[d] = p.O_lo[d]; }
-    a.qchunk = p.fwd.qchunk; a.kspan = p.fwd.kspan;
-    a.R0 = p.R0; a.dR = p.dR;
-    a.bound_pts = (double)p.max_shell_points;
+    fill_forward_args(p, vol, a);
     const bool prof = p.profiling && p.ev_used[0] + 2 <= (int)p.ev[0].size();
     if (prof) cudaEventRecord(p.ev[0][p.ev_used[0]], s);
-    k_brick_gather<kBF><<<(unsigned)p.fwd.items, kFwdThreads, p.fwd.smem, s>>>(a);
+    k_brick_gather<kBF, false><<<(unsigned)p.fwd.items, kFwdThreads, p.fwd.smem, s>>>(a);
     if (prof) { cudaEventRecord(p.ev[0][p.ev_used[0] + 1], s); p.ev_used[0] += 2; }
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_project: k_brick_gather: ") + cudaGetErrorString(e));
@@ -255,53 +273,18 @@ int launch_project(Plan &p, const float *vol, void *data, cudaStream_t s) {
 
 // ---------------------------------------------------------------------------- point counting
 
-struct CountArgs {
-    DevTables t;
-    int nx, ny, nz, K;
-    float O[3], O_lo[3];
-};
-
-__global__ void k_count(CountArgs a, unsigned long long *count) {
-    // every lattice point of every (q, k) with its stencil touching the grid, i.e. its cell in
-    // [-1, n-1]^3; a warp takes 32 consecutive points (one anchor) of a ring at a time
-    const int qk = blockIdx.x;
-    const int q = qk / a.K, k = qk % a.K;
-    const Xdcr &x = a.t.xd[q];
-    const int ck = x.cls * a.K + k;
-    const int nr = a.t.ring_cnt[ck], off = a.t.ring_off[ck];
-    const int lane = threadIdx.x & 31;
-    unsigned long long n = 0;
-    for (int i = threadIdx.x >> 5; i < nr; i += blockDim.x >> 5) {
-        const Ring r = a.t.rings[off + i];
-        for (int j0 = 0; j0 < r.nj; j0 += 32) {
-            int I[3];
-            float f[3];
-            anchor_point(a.O, a.O_lo, x, r.h, r.h_lo, a.t.anchors[r.aoff + (j0 >> kAnchorShift)], I, f);
-            if (j0 + lane >= r.nj) continue;
-            const float3 R = anchor_offset(f, a.t.anchors[r.aoff + (j0 >> kAnchorShift)].x,
-                                           a.t.anchors[r.aoff + (j0 >> kAnchorShift)].z, x.ex, x.ey, r.dphi, r.dphi_lo,
-                                           r.poly, lane);
-            const int cx = I[0] + (int)floorf(R.x), cy = I[1] + (int)floorf(R.y), cz = I[2] + (int)floorf(R.z);
-            n += (cx >= -1 && cx < a.nx && cy >= -1 && cy < a.ny && cz >= -1 && cz < a.nz);
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
-    if (lane == 0 && n) atomicAdd(count, n);
-}
-
+// Lattice points whose stencil touches the grid: the projector's enumeration in COUNT mode.
 int count_grid_points(Plan &p, long long *out) {
-    CountArgs a;
-    a.t = p.t;
-    a.nx = p.nx; a.ny = p.ny; a.nz = p.nz; a.K = p.K;
-    for (int d = 0; d < 3; ++d) { a.O[d] = p.O[d]; a.O_lo[d] = p.O_lo[d]; }
-    unsigned long long *d = (unsigned long long *)p.d_count;
-    cudaError_t e = cudaMemset(d, 0, sizeof(unsigned long long));
+    FwdArgs a;
+    fill_forward_args(p, nullptr, a);
+    a.count = p.d_count;
+    cudaError_t e = cudaMemset(p.d_count, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) {
-        k_count<<<(unsigned)((size_t)p.Q * p.K), 256>>>(a, d);
+        k_brick_gather<kBF, true><<<(unsigned)p.fwd.items, kFwdThreads, p.fwd.smem>>>(a);
         e = cudaGetLastError();
     }
     unsigned long long h = 0;
-    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, p.d_count, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_plan_query: count: ") + cudaGetErrorString(e));
     *out = (long long)h;
     return OAT_OK;
