@@ -175,6 +175,44 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_pls(args):
+    """PLS-TV (FISTA-TV, x >= 0) from zero to a 1e-3 relative data residual on the 160^3
+    workload: 96 rings x 90 views on 50 mm, K = 1024, 120 ellipsoids, noise-free data u = H alpha.
+    mu = 1e-6 L; the TV prox takes 5 FGP iterations.  GPU time by CUDA events (the step-size
+    estimate, 20 power iterations, is reported separately)."""
+    import torch
+    from paper_1304_2017_gb300 import oat
+    from paper_1304_2017_gb300 import workloads as W
+    from paper_1304_2017_gb300.fista import FistaTV
+    torch.cuda.set_device(0)
+    geom = W.config("c3")
+    plan = oat.Plan(geom)
+    alpha = torch.from_numpy(W.phantom("c3", geom)).cuda()
+    u = plan.project(alpha).clone()
+    solver = FistaTV(plan, mu=0.0, inner=5)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    L = solver.lipschitz(iters=20)
+    e1.record()
+    torch.cuda.synchronize()
+    l_s = e0.elapsed_time(e1) * 1e-3
+    solver.mu = 1e-6 * L
+    _, info = solver.solve(u, iters=args.pls_iters, tol=1e-3)
+    r = info["residual"]
+    k = next((i for i, v in enumerate(r) if v <= 1e-3), None)
+    t = info["gpu_seconds"][k] if k is not None else None
+    st = plan.stats(count_grid_points=True)
+    line = {"metric": "PLS-TV GPU seconds to a 1e-3 relative data residual (zero start)", "value": t, "unit": "s",
+            "higher_is_better": False, "iterations": (k + 1) if k is not None else None,
+            "final_residual": r[-1], "seconds_per_iteration": info["gpu_seconds"][-1] / len(r),
+            "step_size_estimate_s": l_s, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "160^3 @ 0.25 mm, 120 ellipsoids, 96 rings x 90 views (8640 transducers) on 50 mm, "
+                                   "K=1024 @ 20 MHz, c=1.5, noise-free", "mu": solver.mu, "L": L, "inner": 5,
+                       "points_per_operator": st["points_grid"]}}
+    plan.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_learned(args):
     """PLS-TV time to a 1e-3 relative data residual from zero and from the learned warm start."""
     from paper_1304_2017_gb300 import warmstart
@@ -220,6 +258,9 @@ def main():
     ap.add_argument("--learned", action="store_true",
                     help="learned warm start: train the U-Net on PLS-TV targets, compare time to a 1e-3 residual")
     ap.add_argument("--learned-args", default="", help="k=v,... overrides for warmstart.run (e.g. n_train=8)")
+    ap.add_argument("--pls", action="store_true",
+                    help="PLS-TV (FISTA-TV) time to a 1e-3 relative data residual on the 160^3 workload")
+    ap.add_argument("--pls-iters", type=int, default=400, help="iteration cap of --pls")
     ap.add_argument("--capture", action="store_true",
                     help="small case for ncu captures: the 256^3 workload on 64 transducers, H and H^T twice")
     args = ap.parse_args()
@@ -229,6 +270,8 @@ def main():
         return run_capture()
     if args.learned:
         return run_learned(args)
+    if args.pls:
+        return run_pls(args)
 
     import torch
     import torch.distributed as dist
