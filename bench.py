@@ -49,6 +49,33 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def _counters():
+    """Per-kernel ncu counters committed under profiles/ (None where not measured)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "counters.json")) as f:
+            return {k: v for k, v in json.load(f).items() if not k.startswith("_")}
+    except (OSError, ValueError):
+        return {}
+
+
+def l2_read_gbs(dev, mb=48, reps=100):
+    """L2 read bandwidth: oat_probe_read over a 48 MB buffer (resident in the 129 MB L2 after a
+    warm-up pass), 16-byte loads cached in L2 only, timed with CUDA events."""
+    import torch
+    from paper_1304_2017_gb300 import oat
+    n = mb * (1 << 20)
+    buf = torch.ones(n // 4, device=dev)
+    sink = torch.zeros(1, device=dev)
+    s = torch.cuda.current_stream(dev).cuda_stream
+    oat.oat_probe_read(buf.data_ptr(), n, 2, sink.data_ptr(), s)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    oat.oat_probe_read(buf.data_ptr(), n, reps, sink.data_ptr(), s)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    return n * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -135,9 +162,22 @@ def cpu_baseline(geom, alpha, y, n_xdcr=32, points_per_xdcr=None):
     oracle.Ht(sub, ys)
     dt = time.perf_counter() - t0
     pts = points_per_xdcr * n_xdcr if points_per_xdcr is not None else oracle.count_points(sub)[1]
+    # one thread, one transducer
+    one = geom.subset(qs[:1])
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.H(one, a64)
+        oracle.Ht(one, ys[:1])
+        dt1 = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(threads)
+    pts1 = oracle.count_points(one)[1]
     return {"value": 2.0 * pts / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{n_xdcr} of {geom.n_transducers} transducers (evenly spaced), full grid and time window; "
-                      f"one H + one H^T in FP64, {dt:.1f} s"}
+                      f"one H + one H^T in FP64, {dt:.1f} s",
+            "single_thread": {"value": 2.0 * pts1 / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"transducer {int(qs[0])}, one H + one H^T in FP64, {dt1:.1f} s"}}
 
 
 def run_reference(args):
@@ -213,6 +253,54 @@ def run_pls(args):
     print(json.dumps(line), flush=True)
 
 
+def run_fbp(args):
+    """Filtered backprojection (Eq. disfbp) on the 256^3 / 23,040-transducer / K = 1536 workload:
+    seconds per reconstruction and voxel-transducer pairs per second, CUDA events around W
+    untimed and K timed calls; the FP64 reference timed on a 16-transducer sample."""
+    import torch
+    from paper_1304_2017_gb300 import oat
+    from paper_1304_2017_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    geom = W.config(args.config)
+    n_r, n_v = (128, 180) if args.config == "c2" else (None, None)
+    pos = geom.positions_mm
+    rs = np.linalg.norm(pos, axis=1)
+    theta = np.arccos(np.clip(pos[:, 2] / rs, -1.0, 1.0))
+    w = rs * (np.pi / n_r) * (2.0 * np.pi / n_v) * np.sin(theta)      # patch area / R^s
+    plan = oat.Plan(geom)
+    plan.set_fbp_weights(w)
+    p = torch.from_numpy(W.random_data(geom, seed=7)).to(dev)
+    out = torch.empty(plan.vol_shape, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        plan.fbp(p, out=out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record()
+    for _ in range(args.steps):
+        plan.fbp(p, out=out)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    sec = e0.elapsed_time(e1) * 1e-3 / args.steps
+    pairs = float(geom.n_voxels) * geom.n_transducers
+    line = {"metric": "FBP voxel-transducer pairs/s (filtered backprojection, Eq. disfbp)", "value": pairs / sec,
+            "unit": "pairs/s", "seconds_per_fbp": sec, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "pairs": pairs}}
+    if not args.no_cpu_baseline:
+        import oracle.fbp as F
+        qs = np.linspace(0, geom.n_transducers - 1, 16).round().astype(int)
+        sub = geom.subset(qs)
+        t0 = time.perf_counter()
+        F.fbp(sub, p[qs].cpu().numpy(), w[qs])
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": float(geom.n_voxels) * len(qs) / dt, "unit": "pairs/s", "cores": 1,
+                                "kind": "oracle", "sample": f"16 of {geom.n_transducers} transducers, full grid, "
+                                                            f"numpy FP64, {dt:.1f} s"}
+    plan.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_learned(args):
     """PLS-TV time to a 1e-3 relative data residual from zero and from the learned warm start."""
     from paper_1304_2017_gb300 import warmstart
@@ -258,6 +346,8 @@ def main():
     ap.add_argument("--learned", action="store_true",
                     help="learned warm start: train the U-Net on PLS-TV targets, compare time to a 1e-3 residual")
     ap.add_argument("--learned-args", default="", help="k=v,... overrides for warmstart.run (e.g. n_train=8)")
+    ap.add_argument("--fbp", action="store_true",
+                    help="filtered backprojection throughput on the 256^3 / 23,040-transducer workload")
     ap.add_argument("--pls", action="store_true",
                     help="PLS-TV (FISTA-TV) time to a 1e-3 relative data residual on the 160^3 workload")
     ap.add_argument("--pls-iters", type=int, default=400, help="iteration cap of --pls")
@@ -272,6 +362,8 @@ def main():
         return run_learned(args)
     if args.pls:
         return run_pls(args)
+    if args.fbp:
+        return run_fbp(args)
 
     import torch
     import torch.distributed as dist
@@ -359,18 +451,27 @@ def main():
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = FLOP_PER_SAMPLE * pts / (dom_ms * 1e-3) / 1e12
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        try:
-            with open(tpath) as f:
-                traffic = json.load(f).get(dom_name.split()[0])
-        except (OSError, ValueError):
-            traffic = None
+    counters = _counters().get(dom_name.split()[0], {})
+    traffic = counters.get("dram_bytes_per_launch")
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": achieved / peak_tflops, "traffic": traffic, "kernel": dom_name,
             "kernel_ms": dom_ms, "peak_source": f"{src}: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
             "flop_per_sample": FLOP_PER_SAMPLE}
+    # on-chip bounds of the dominant kernel: instruction issue (4 warp instructions per clock per
+    # SM) at its measured instruction count, and L2 bytes against a measured L2 copy bandwidth
+    onchip = {}
+    ips = counters.get("warp_instructions_per_sample")
+    if ips:
+        bound = N_SM * 4 * sm_max * 1e6 / ips
+        onchip["issue"] = {"warp_instructions_per_sample": ips, "bound_samples_per_s": bound,
+                           "achieved_samples_per_s": pts / (dom_ms * 1e-3), "frac": pts / (dom_ms * 1e-3) / bound}
+    l2_peak = l2_read_gbs(dev)
+    lts = counters.get("lts_bytes_per_launch")
+    onchip["l2"] = {"peak_gbs": l2_peak, "peak_source": "measured here: oat_probe_read over a 48 MB L2-resident buffer",
+                    "achieved_gbs": (lts / (dom_ms * 1e-3) / 1e9) if lts else None}
+    if lts:
+        onchip["l2"]["frac"] = onchip["l2"]["achieved_gbs"] / l2_peak
+    onchip["counters_source"] = "profiles/counters.json (ncu, one pass at full size; instructions from the --set full capture)"
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -382,7 +483,7 @@ def main():
             "gpu_launches": args.steps * LAUNCHES_PER_STEP,
             "kernel_ms": {"k_brick_gather": g_ms / max(g_n, 1), "k_brick_gather_t": b_ms / max(b_n, 1)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
-            "roofline": roof, "clocks": clocks}
+            "roofline": roof, "onchip": onchip, "clocks": clocks}
     if rank == 0 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline(geom, alpha_np, y_np, n_xdcr=int(os.environ.get("OAT_CPU_XDCR", "16")))

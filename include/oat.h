@@ -150,6 +150,24 @@ int oat_backproject(oat_plan plan, const void *d_data, float *d_vol, void *strea
 int oat_backproject_noalloc(oat_plan plan, const void *d_data, float *d_vol, void *stream);
 
 /*
+ * Filtered backprojection (Sec. III.C, Eqs. linearint and disfbp): for every node n,
+ *   alpha_n = -1 / (pi Gamma c dt) * sum_q w_q { 0.5 (p_{q,k+1} - p_{q,k})
+ *                                   + [p_{q,k} + (k~ - k)(p_{q,k+1} - p_{q,k})] / (k~ + t_min/dt) },
+ *   k~ = (|r_q - r_n| / c - t_min) / dt, k = floor(k~)
+ * (the same sum as the paper's Eq. disfbp), samples outside 0 .. K-1 counting as zero.
+ *
+ * oat_plan_set_fbp_weights: w_q, one per transducer (host array of n_transducers doubles; for a
+ *   spherical scan, the patch area over the sphere radius, R^s dtheta dphi sin theta_q).  Copied
+ *   into the plan (synchronous); required before oat_fbp.
+ * oat_fbp: d_data [Q][K] in the plan's data dtype -> d_vol [nz][ny][nx] float32 (overwritten);
+ *   asynchronous on `stream`, allocates nothing.  Both 16-byte aligned.
+ * Errors: OAT_ERR_INVALID_ARG (NULL, misaligned, non-finite weight, weights not set),
+ *         OAT_ERR_CUDA.
+ */
+int oat_plan_set_fbp_weights(oat_plan plan, const double *weights);
+int oat_fbp(oat_plan plan, const void *d_data, float *d_vol, void *stream);
+
+/*
  * Fill *stats.  With count_grid_points != 0 the call also counts, on the device and
  * synchronously (on the legacy default stream), the lattice points whose interpolation
  * stencil touches the grid, the unit of work of the throughput metric.
@@ -160,9 +178,10 @@ int oat_plan_query(oat_plan plan, int count_grid_points, oat_stats *stats);
 /*
  * Kernel timing for measurement.  With enable != 0 every later oat_project and
  * oat_backproject records a pair of CUDA events on the caller's stream around its main
- * kernel (the shell gather of G, the voxel gather of G^T).  oat_plan_kernel_time()
- * synchronises on those events and returns the summed milliseconds and the number of
- * launches for which = 0 (G) or 1 (G^T) since the last reset (reset != 0 clears them).
+ * kernel (the shell gather of G, the voxel gather of G^T; oat_fbp likewise).
+ * oat_plan_kernel_time() synchronises on those events and returns the summed milliseconds and
+ * the number of launches for which = 0 (G), 1 (G^T) or 2 (FBP) since the last reset
+ * (reset != 0 clears them).
  * At most 4096 launches are recorded per kernel between resets; later ones are not timed.
  * Errors: OAT_ERR_INVALID_ARG, OAT_ERR_CUDA.
  */

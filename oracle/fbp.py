@@ -43,8 +43,9 @@ def arc_weights(positions_mm, n_rings, n_views):
     return rs * (math.pi / n_rings) * (2.0 * math.pi / n_views) * np.sin(theta)
 
 
-def fbp(geom, p, weights):
-    """alpha_fbp on the node grid of `geom` (nz, ny, nx) from data p [Q][K] (Eq. disfbp)."""
+def fbp(geom, p, weights, nodes=None):
+    """alpha_fbp from data p [Q][K] (Eq. disfbp): on the whole node grid of `geom` as
+    (nz, ny, nx), or at the nodes given as (ix, iy, iz) triples (a 1-D array)."""
     p = np.asarray(p, np.float64).reshape(geom.data_shape)
     w = np.asarray(weights, np.float64).reshape(geom.n_transducers)
     dt = 1.0 / geom.fs_mhz
@@ -52,13 +53,18 @@ def fbp(geom, p, weights):
     tau0 = geom.t_min_us / dt
     K = geom.n_samples
     xs, ys, zs = geom.node_coords_mm()
-    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
-    acc = np.zeros(geom.vol_shape)
+    if nodes is None:
+        Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    else:
+        nd = np.asarray(nodes, np.int64).reshape(-1, 3)
+        X, Y, Z = xs[nd[:, 0]], ys[nd[:, 1]], zs[nd[:, 2]]
+    acc = np.zeros(X.shape)
     for q in range(geom.n_transducers):
         rq = geom.positions_mm[q]
         dist = np.sqrt((X - rq[0]) ** 2 + (Y - rq[1]) ** 2 + (Z - rq[2]) ** 2)
         kt = (dist / c - geom.t_min_us) / dt                 # k~
         k = np.floor(kt).astype(np.int64)
+
         def sample(j):
             inside = (j >= 0) & (j < K)
             return np.where(inside, p[q, np.clip(j, 0, K - 1)], 0.0)

@@ -18,7 +18,7 @@ LIB = os.path.join(PKG, "liboat.so")
 ROOT = os.path.dirname(PKG)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["abi.cpp", "plan.cpp", "forward.cu", "adjoint.cu", "recon.cu", "unet.cu"]
+SOURCES = ["abi.cpp", "plan.cpp", "forward.cu", "adjoint.cu", "recon.cu", "unet.cu", "probe.cu", "fbp.cu"]
 
 
 def nvcc() -> str:
@@ -37,7 +37,7 @@ def _compile(src: str) -> str:
     obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ".o")
     path = os.path.join(SRC, src)
     deps = [path, os.path.join(SRC, "oat_internal.h"), os.path.join(SRC, "brick.cuh"), os.path.join(ROOT, "include", "oat.h"),
-            os.path.join(ROOT, "include", "oat_recon.h"), os.path.join(ROOT, "include", "oat_unet.h")]
+            os.path.join(ROOT, "include", "oat_recon.h"), os.path.join(ROOT, "include", "oat_unet.h"), os.path.join(ROOT, "include", "oat_probe.h")]
     if os.path.exists(obj) and all(os.path.getmtime(obj) >= os.path.getmtime(d) for d in deps):
         return obj
     subprocess.check_call([nvcc()] + _flags() + ["-c", path, "-o", obj])

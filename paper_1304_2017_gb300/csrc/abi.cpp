@@ -2,6 +2,7 @@
 // error reporting.  All arithmetic lives in the kernels (forward.cu, adjoint.cu) and the
 // plan builder (plan.cpp).
 #include <cstdint>
+#include <cmath>
 #include <string>
 
 #include "oat_internal.h"
@@ -95,6 +96,31 @@ int oat_backproject_noalloc(oat_plan plan, const void *d_data, float *d_vol, voi
     return launch_backproject_static(*p, d_data, d_vol, (cudaStream_t)stream);
 }
 
+int oat_plan_set_fbp_weights(oat_plan plan, const double *weights) {
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || !weights) return set_error(OAT_ERR_INVALID_ARG, "oat_plan_set_fbp_weights: NULL plan or weights");
+    for (int q = 0; q < p->Q; ++q)
+        if (!std::isfinite(weights[q])) return set_error(OAT_ERR_INVALID_ARG, "oat_plan_set_fbp_weights: non-finite weight");
+    DeviceGuard dg(p->device);
+    if (dg.err != cudaSuccess)
+        return set_error(OAT_ERR_CUDA, std::string("oat_plan_set_fbp_weights: ") + cudaGetErrorString(dg.err));
+    for (int q = 0; q < p->Q; ++q) p->fbp_host[2 * (size_t)q].w = (float)weights[q];
+    cudaError_t e = cudaMemcpy(p->d_fbp, p->fbp_host.data(), sizeof(float4) * p->fbp_host.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_plan_set_fbp_weights: ") + cudaGetErrorString(e));
+    p->fbp_weights = true;
+    return OAT_OK;
+}
+
+int oat_fbp(oat_plan plan, const void *d_data, float *d_vol, void *stream) {
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || !d_vol || !d_data) return set_error(OAT_ERR_INVALID_ARG, "oat_fbp: NULL plan or buffer");
+    if (!aligned16(d_vol) || !aligned16(d_data)) return set_error(OAT_ERR_INVALID_ARG, "oat_fbp: buffers must be 16-byte aligned");
+    if (!p->fbp_weights) return set_error(OAT_ERR_INVALID_ARG, "oat_fbp: weights not set (oat_plan_set_fbp_weights)");
+    DeviceGuard dg(p->device);
+    if (dg.err != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_fbp: ") + cudaGetErrorString(dg.err));
+    return launch_fbp(*p, d_data, d_vol, (cudaStream_t)stream);
+}
+
 int oat_plan_query(oat_plan plan, int want_count, oat_stats *st) {
     Plan *p = reinterpret_cast<Plan *>(plan);
     if (!p || !st) return set_error(OAT_ERR_INVALID_ARG, "oat_plan_query: NULL plan or stats");
@@ -121,7 +147,7 @@ int oat_plan_set_profiling(oat_plan plan, int enable) {
     if (!p) return set_error(OAT_ERR_INVALID_ARG, "oat_plan_set_profiling: NULL plan");
     if (enable && p->ev[0].empty()) {
         DeviceGuard dg(p->device);
-        for (int w = 0; w < 2; ++w) {
+        for (int w = 0; w < 3; ++w) {
             p->ev[w].resize(2 * kMaxEvents);
             for (auto &e : p->ev[w]) {
                 cudaError_t err = cudaEventCreate(&e);
@@ -135,7 +161,7 @@ int oat_plan_set_profiling(oat_plan plan, int enable) {
 
 int oat_plan_kernel_time(oat_plan plan, int which, int reset, double *ms, long long *launches) {
     Plan *p = reinterpret_cast<Plan *>(plan);
-    if (!p || which < 0 || which > 1) return set_error(OAT_ERR_INVALID_ARG, "oat_plan_kernel_time: bad plan or kernel index");
+    if (!p || which < 0 || which > 2) return set_error(OAT_ERR_INVALID_ARG, "oat_plan_kernel_time: bad plan or kernel index");
     DeviceGuard dg(p->device);
     for (int i = 0; i + 1 < p->ev_used[which]; i += 2) {
         cudaError_t e = cudaEventSynchronize(p->ev[which][i + 1]);

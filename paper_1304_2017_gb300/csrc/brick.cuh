@@ -21,7 +21,7 @@ namespace oat {
 constexpr float kTwoPiF = 6.28318530717958647692f;
 
 // Brick seen from one transducer (local frame of the transducer, index units).
-struct BrickView {
+struct __align__(16) BrickView {
     float ex[3], ey[3], ez[3];
     float wz0;     // (c - O) . e_z : axial coordinate of the centre about the global origin
     float rw;      // distance of the centre from the transducer axis
@@ -187,7 +187,7 @@ __device__ __forceinline__ int unit_ring(int fi, int T, int p0, int p1, int p2, 
 }
 
 // One anchor segment of a warp's chunk.
-struct SegSlot {
+struct __align__(16) SegSlot {
     float f[3];          // anchor fraction A - I
     int I[3];            // anchor cell I, relative to the brick's lowest cell L
     float xa, ya;        // anchor local coordinates (hi parts)

@@ -1,0 +1,159 @@
+// Filtered backprojection (include/oat.h, Sec. III.C, Eq. disfbp): a per-voxel gather over all
+// transducers with two-tap linear interpolation in time and the first difference for dp/dt.
+//
+// k_fbp  one thread block per brick of 8^3 voxels, one voxel per thread.  Transducers come in
+//        tiles of 256 through shared memory; for each (brick, transducer) one thread computes,
+//        in float-pair arithmetic, the distance D from the transducer to the brick centre and
+//        the fractional sample index K = D ds / (c dt) - t_min / dt split into an integer and an
+//        FP32 fraction.  A voxel at offset delta from the centre is at distance D + dD with
+//          dD = (2 D u.delta + |delta|^2) / (D + sqrt(D^2 + 2 D u.delta + |delta|^2))
+//        (u the unit vector from the transducer to the centre): every FP32 quantity stays
+//        small, so k~ = K + dD ds / (c dt) keeps about 1e-6 of a sample, as the interpolation
+//        weight needs.  Per term, with w = k~ - k and tau = k~ + t_min / dt,
+//          {..} = 0.5 (p_{k+1} - p_k) + (p_k + w (p_{k+1} - p_k)) / tau
+//        (the braces of Eq. disfbp rewritten), summed with compensation over a tile and in
+//        double across tiles; every voxel is written once.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cmath>
+#include <string>
+
+#include "oat_internal.h"
+
+namespace oat {
+
+constexpr int kFbpB = 8;
+constexpr int kFbpThreads = kFbpB * kFbpB * kFbpB;
+constexpr int kFbpTile = 256;
+
+struct FbpArgs {
+    const float4 *xd;            // [2Q]: (T hi, w), (T lo, 0); T in index units from node (0,0,0)
+    const void *p;               // [Q][K]
+    float *vol;                  // [nz][ny][nx]
+    int nx, ny, nz, K, Q;
+    int bx, by;                  // bricks along x and y
+    float sk_hi, sk_lo;          // ds / (c dt): index units -> samples, as a float pair
+    float t0_hi, t0_lo;          // t_min / dt as a float pair
+    double scale;                // -1 / (pi Gamma c dt)
+};
+
+// Per (brick, transducer): unit vector u, distance D (index units), integer and fractional part
+// of the sample index at the brick centre, tau at the centre, weight.
+struct __align__(16) FbpQ {
+    float ux, uy, uz, D;
+    int kint;
+    float kfrac, tau, w;
+};
+
+template <int DT>
+__device__ __forceinline__ float load_p(const void *p, size_t i) {
+    if (DT == OAT_F32) return __ldg((const float *)p + i);
+    else if (DT == OAT_F16) return __half2float(((const __half *)p)[i]);
+    else return __bfloat162float(((const __nv_bfloat16 *)p)[i]);
+}
+
+__device__ __forceinline__ FbpQ fbp_setup(const FbpArgs &a, int q, float cx, float cy, float cz) {
+    const float4 hi = __ldg(a.xd + 2 * q), lo = __ldg(a.xd + 2 * q + 1);
+    const float c[3] = {cx, cy, cz}, th[3] = {hi.x, hi.y, hi.z}, tl[3] = {lo.x, lo.y, lo.z};
+    // v = c - T and S + E = |v|^2, float pairs
+    float vh[3], S = 0.f, E = 0.f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        float s, e;
+        two_sum(c[d], -th[d], s, e);
+        e = __fsub_rn(e, tl[d]);
+        vh[d] = s;
+        const float pp = __fmul_rn(s, s);
+        const float pe = fmaf(__fmul_rn(2.f, s), e, fmaf(s, s, -pp));
+        float t;
+        two_sum(S, pp, S, t);
+        E = __fadd_rn(E, __fadd_rn(t, pe));
+    }
+    // D = sqrt(S + E) as D0 + corr (one Newton step in float pairs)
+    const float D0 = sqrtf(S);
+    const float r = __fmul_rn(D0, D0), re = fmaf(D0, D0, -r);
+    const float corr = __fdiv_rn(__fadd_rn(__fsub_rn(__fsub_rn(S, r), re), E), __fmul_rn(2.f, D0));
+    // K = D sk - t0
+    const float kp = __fmul_rn(D0, a.sk_hi);
+    const float kpe = fmaf(corr, a.sk_hi, fmaf(D0, a.sk_lo, fmaf(D0, a.sk_hi, -kp)));
+    float ks, ke;
+    two_sum(kp, -a.t0_hi, ks, ke);
+    ke = __fadd_rn(ke, __fsub_rn(kpe, a.t0_lo));
+    const float fl = floorf(ks);
+    FbpQ o;
+    const float inv = __fdiv_rn(1.f, D0);
+    o.ux = __fmul_rn(vh[0], inv); o.uy = __fmul_rn(vh[1], inv); o.uz = __fmul_rn(vh[2], inv);
+    o.D = D0;
+    o.kint = (int)fl;
+    o.kfrac = __fadd_rn(__fsub_rn(ks, fl), ke);
+    o.tau = __fadd_rn(kp, kpe);
+    o.w = hi.w;
+    return o;
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kFbpThreads) k_fbp(FbpArgs a) {
+    __shared__ FbpQ tq[kFbpTile];
+    const int b = blockIdx.x;
+    const int bx = b % a.bx, by = (b / a.bx) % a.by, bz = b / (a.bx * a.by);
+    const int lx = threadIdx.x & 7, ly = (threadIdx.x >> 3) & 7, lz = threadIdx.x >> 6;
+    const int ix = bx * kFbpB + lx, iy = by * kFbpB + ly, iz = bz * kFbpB + lz;
+    const float cx = bx * kFbpB + 3.5f, cy = by * kFbpB + 3.5f, cz = bz * kFbpB + 3.5f;
+    const float dx = lx - 3.5f, dy = ly - 3.5f, dz = lz - 3.5f;
+    const float dd = dx * dx + dy * dy + dz * dz;
+    const float sk = a.sk_hi;
+    double total = 0.0;
+    for (int q0 = 0; q0 < a.Q; q0 += kFbpTile) {
+        const int nt = min(kFbpTile, a.Q - q0);
+        __syncthreads();
+        if (threadIdx.x < nt) tq[threadIdx.x] = fbp_setup(a, q0 + threadIdx.x, cx, cy, cz);
+        __syncthreads();
+        float s = 0.f, e = 0.f;
+        for (int t = 0; t < nt; ++t) {
+            const FbpQ Q = tq[t];
+            const float ud = fmaf(Q.uz, dz, fmaf(Q.uy, dy, Q.ux * dx));
+            const float tt = fmaf(2.f * Q.D, ud, dd);
+            const float sq = sqrtf(fmaf(Q.D, Q.D, tt));
+            const float dD = __fdividef(tt, Q.D + sq);                 // distance - D
+            const float kf = fmaf(dD, sk, Q.kfrac);
+            const float fk = floorf(kf);
+            const int k = Q.kint + (int)fk;
+            const float wgt = kf - fk;
+            const float tau = fmaf(dD, sk, Q.tau);
+            const size_t row = (size_t)(q0 + t) * a.K;
+            const float p0 = (k >= 0 && k < a.K) ? load_p<DT>(a.p, row + k) : 0.f;
+            const float p1 = (k + 1 >= 0 && k + 1 < a.K) ? load_p<DT>(a.p, row + k + 1) : 0.f;
+            const float dp = p1 - p0;
+            const float br = fmaf(fmaf(wgt, dp, p0), __frcp_rn(tau), 0.5f * dp);
+            kadd(s, e, Q.w * br);
+        }
+        total += (double)s + (double)e;
+    }
+    if (ix < a.nx && iy < a.ny && iz < a.nz) a.vol[((size_t)iz * a.ny + iy) * a.nx + ix] = (float)(total * a.scale);
+}
+
+int launch_fbp(Plan &p, const void *data, float *vol, cudaStream_t s) {
+    FbpArgs a;
+    a.xd = p.d_fbp; a.p = data; a.vol = vol;
+    a.nx = p.nx; a.ny = p.ny; a.nz = p.nz; a.K = p.K; a.Q = p.Q;
+    a.bx = (p.nx + kFbpB - 1) / kFbpB; a.by = (p.ny + kFbpB - 1) / kFbpB;
+    const int bz = (p.nz + kFbpB - 1) / kFbpB;
+    const double sk = p.g.spacing_mm / (p.g.c_mm_per_us * p.dt), t0 = p.g.t_min_us / p.dt;
+    a.sk_hi = (float)sk; a.sk_lo = (float)(sk - (double)a.sk_hi);
+    a.t0_hi = (float)t0; a.t0_lo = (float)(t0 - (double)a.t0_hi);
+    a.scale = -1.0 / (M_PI * p.g.gruneisen * p.g.c_mm_per_us * p.dt);
+    const unsigned blocks = (unsigned)((size_t)a.bx * a.by * bz);
+    const bool prof = p.profiling && p.ev_used[2] + 2 <= (int)p.ev[2].size();
+    if (prof) cudaEventRecord(p.ev[2][p.ev_used[2]], s);
+    switch (p.g.data_dtype) {
+        case OAT_F32: k_fbp<OAT_F32><<<blocks, kFbpThreads, 0, s>>>(a); break;
+        case OAT_F16: k_fbp<OAT_F16><<<blocks, kFbpThreads, 0, s>>>(a); break;
+        default: k_fbp<OAT_BF16><<<blocks, kFbpThreads, 0, s>>>(a); break;
+    }
+    if (prof) { cudaEventRecord(p.ev[2][p.ev_used[2] + 1], s); p.ev_used[2] += 2; }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? OAT_OK : set_error(OAT_ERR_CUDA, std::string("oat_fbp: k_fbp: ") + cudaGetErrorString(e));
+}
+
+}  // namespace oat

@@ -31,7 +31,7 @@ namespace oat {
 constexpr int kAnchorShift = 5;                      // one anchor every 32 points of a ring
 constexpr int kAnchorMask = (1 << kAnchorShift) - 1;
 
-struct Ring {
+struct __align__(16) Ring {
     float h, a, dphi;
     int nj;
     float h_lo, dphi_lo;
@@ -40,12 +40,12 @@ struct Ring {
 };
 
 // Per-transducer record: local frame (float pairs hi + lo) and |r_q| / Delta_s, radius class.
-struct Xdcr {
+struct __align__(16) Xdcr {
     float ex[3], ey[3], ez[3];
     float ex_lo[3], ey_lo[3], ez_lo[3];
     float dist;   // |r_q| / Delta_s
     int cls;
-    int pad[2];
+    int pad[3];
 };
 
 struct DevTables {
@@ -103,10 +103,16 @@ struct Plan {
 
     // profiling
     bool profiling = false;
-    std::vector<cudaEvent_t> ev[2];
-    int ev_used[2] = {0, 0};
-    double ms_acc[2] = {0, 0};
-    long long launches[2] = {0, 0};
+    std::vector<cudaEvent_t> ev[3];       // [G, G^T, FBP]
+    int ev_used[3] = {0, 0, 0};
+    double ms_acc[3] = {0, 0, 0};
+    long long launches[3] = {0, 0, 0};
+
+    // filtered backprojection: per transducer (T hi xyz, weight) and (T lo xyz, 0), T the
+    // position in index units relative to node (0,0,0) as a float pair
+    float4 *d_fbp = nullptr;
+    std::vector<float4> fbp_host;
+    bool fbp_weights = false;
 };
 
 // status helpers (abi.cpp)
@@ -117,6 +123,7 @@ int launch_project(Plan &p, const float *vol, void *data, cudaStream_t s);
 int launch_backproject(Plan &p, const void *data, float *vol, cudaStream_t s);
 int launch_backproject_static(Plan &p, const void *data, float *vol, cudaStream_t s);
 int count_grid_points(Plan &p, long long *out);
+int launch_fbp(Plan &p, const void *data, float *vol, cudaStream_t s);
 int set_adjoint_attributes();
 int set_forward_attributes();
 size_t forward_smem_bytes();

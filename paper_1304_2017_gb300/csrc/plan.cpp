@@ -280,6 +280,7 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
         if (p->d_gacc) cudaFree(p->d_gacc);
         if (p->d_vacc) cudaFree(p->d_vacc);
         if (p->d_amax) cudaFree(p->d_amax);
+        if (p->d_fbp) cudaFree(p->d_fbp);
         delete p;
         cudaGetLastError();
         cudaSetDevice(prev);
@@ -293,8 +294,20 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
     if ((e = cudaMalloc(&p->d_gacc, g_bytes)) != cudaSuccess) return fail(e, "cudaMalloc(G scratch)");
     if ((e = cudaMalloc(&p->d_vacc, v_bytes)) != cudaSuccess) return fail(e, "cudaMalloc(G^T scratch)");
     if ((e = cudaMalloc(&p->d_amax, 256)) != cudaSuccess) return fail(e, "cudaMalloc(scale scratch)");
+    // FBP table: transducer positions in index units as float pairs; weights set later
+    p->fbp_host.resize(2 * (size_t)Q);
+    for (int q = 0; q < Q; ++q) {
+        float hi[3], lo[3];
+        for (int d = 0; d < 3; ++d) split((p->pos[3 * q + d] - g.origin_mm[d]) / ds, hi[d], lo[d]);
+        p->fbp_host[2 * q] = make_float4(hi[0], hi[1], hi[2], 0.f);
+        p->fbp_host[2 * q + 1] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    }
+    if ((e = cudaMalloc(&p->d_fbp, sizeof(float4) * p->fbp_host.size())) != cudaSuccess) return fail(e, "cudaMalloc(FBP table)");
+    if ((e = cudaMemcpy(p->d_fbp, p->fbp_host.data(), sizeof(float4) * p->fbp_host.size(), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return fail(e, "cudaMemcpy(FBP table)");
     p->d_count = (unsigned long long *)((char *)p->d_amax + 128);
-    p->scratch_bytes = (long long)(g_bytes + v_bytes + 256);
+    p->scratch_bytes = (long long)(g_bytes + v_bytes + 256 + sizeof(float4) * p->fbp_host.size());
     if (set_forward_attributes() != OAT_OK || set_adjoint_attributes() != OAT_OK) {
         std::string msg = std::string("oat_plan_create: ") + oat_last_error();
         fail(cudaSuccess, "kernel attributes");
@@ -320,9 +333,10 @@ void plan_destroy(Plan *p) {
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(p->device);
-    for (int w = 0; w < 2; ++w)
+    for (int w = 0; w < 3; ++w)
         for (cudaEvent_t e : p->ev[w]) cudaEventDestroy(e);
     if (p->d_tables) cudaFree(p->d_tables);
+    if (p->d_fbp) cudaFree(p->d_fbp);
     if (p->d_gacc) cudaFree(p->d_gacc);
     if (p->d_vacc) cudaFree(p->d_vacc);
     if (p->d_amax) cudaFree(p->d_amax);

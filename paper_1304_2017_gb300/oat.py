@@ -56,6 +56,8 @@ def _load():
     lib.oat_project.argtypes = [vp, vp, vp, vp]
     lib.oat_backproject.argtypes = [vp, vp, vp, vp]
     lib.oat_backproject_noalloc.argtypes = [vp, vp, vp, vp]
+    lib.oat_plan_set_fbp_weights.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    lib.oat_fbp.argtypes = [vp, vp, vp, vp]
     lib.oat_plan_query.argtypes = [vp, ctypes.c_int, ctypes.POINTER(oat_stats)]
     lib.oat_plan_set_profiling.argtypes = [vp, ctypes.c_int]
     lib.oat_plan_kernel_time.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -66,12 +68,14 @@ def _load():
     lib.oat_fista_momentum.argtypes = [ll, vp, vp, f32, vp, vp]
     lib.oat_dot.argtypes = [ll, vp, vp, vp, vp]
     lib.oat_tv_value.argtypes = [i32, i32, i32, vp, vp, vp]
-    for name in ("oat_fista_residual", "oat_tv_prox", "oat_fista_momentum", "oat_dot", "oat_tv_value"):
+    lib.oat_probe_read.argtypes = [vp, ll, i32, vp, vp]
+    for name in ("oat_fista_residual", "oat_tv_prox", "oat_fista_momentum", "oat_dot", "oat_tv_value",
+                 "oat_probe_read"):
         getattr(lib, name).restype = ctypes.c_int
     lib.oat_last_error.restype = ctypes.c_char_p
     lib.oat_version.restype = ctypes.c_int
     for name in ("oat_plan_create", "oat_plan_destroy", "oat_project", "oat_backproject", "oat_backproject_noalloc",
-                 "oat_plan_query",
+                 "oat_plan_query", "oat_plan_set_fbp_weights", "oat_fbp",
                  "oat_plan_set_profiling", "oat_plan_kernel_time"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
@@ -129,6 +133,15 @@ def oat_backproject_noalloc(handle, d_data, d_vol, stream=0):
                                               ctypes.c_void_p(stream)))
 
 
+def oat_plan_set_fbp_weights(handle, weights):
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    return _check(lib.oat_plan_set_fbp_weights(handle, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+
+def oat_fbp(handle, d_data, d_vol, stream=0):
+    return _check(lib.oat_fbp(handle, ctypes.c_void_p(d_data), ctypes.c_void_p(d_vol), ctypes.c_void_p(stream)))
+
+
 def oat_plan_query(handle, count_grid_points=False):
     st = oat_stats()
     _check(lib.oat_plan_query(handle, int(bool(count_grid_points)), ctypes.byref(st)))
@@ -170,6 +183,10 @@ def oat_dot(n, x, y, acc, stream=0):
 
 def oat_tv_value(nx, ny, nz, x, acc, stream=0):
     return _check(lib.oat_tv_value(nx, ny, nz, _p(x), _p(acc), _p(stream)))
+
+
+def oat_probe_read(buf, n_bytes, reps, sink, stream=0):
+    return _check(lib.oat_probe_read(_p(buf), n_bytes, reps, _p(sink), _p(stream)))
 
 
 # ---- torch wrapper ---------------------------------------------------------------------
@@ -233,6 +250,23 @@ class Plan:
             out = torch.empty(self.data_shape, dtype=self.torch_data_dtype, device=vol.device)
         self._checked(out, self.data_shape, self.torch_data_dtype, "out")
         oat_project(self.handle, vol.data_ptr(), out.data_ptr(), self._stream())
+        return out
+
+    def set_fbp_weights(self, weights):
+        """Per-transducer FBP weights (patch area / sphere radius), n_transducers values."""
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        if w.shape != (self.data_shape[0],):
+            raise ValueError(f"weights: expected {self.data_shape[0]} values, got shape {w.shape}")
+        oat_plan_set_fbp_weights(self.handle, w)
+
+    def fbp(self, data, out=None):
+        """Filtered backprojection of data [Q][K] (plan's data dtype) -> (nz, ny, nx) float32."""
+        torch = self._torch
+        self._checked(data, self.data_shape, self.torch_data_dtype, "data")
+        if out is None:
+            out = torch.empty(self.vol_shape, dtype=torch.float32, device=data.device)
+        self._checked(out, self.vol_shape, torch.float32, "out")
+        oat_fbp(self.handle, data.data_ptr(), out.data_ptr(), self._stream())
         return out
 
     def backproject(self, data, out=None):

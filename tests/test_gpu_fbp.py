@@ -1,0 +1,122 @@
+"""Parity of the sm_103a filtered backprojection (oat_fbp, through the C ABI) with the FP64
+reference oracle/fbp.py (Eq. disfbp).
+
+Tolerance 1e-5 relative L2: per term the kernel keeps the sample position to about 1e-6 of a
+sample (float-pair distance to each brick centre, small FP32 offsets) and sums with
+compensation, so its error stays near FP32 rounding of the data and weights.  FP16 / BF16 data
+are read exactly, so the reference gets the same rounded values.
+
+The data are band-limited, as measured pressure is: seeded Gaussian pulses several samples wide,
+or the forward model's own data.  Eq. disfbp is discontinuous in the sample position -- where
+k~ crosses an integer the one-sided difference p_{k+1} - p_k moves to the next pair -- so any
+rounding difference that moves k~ across an integer changes the term by the second difference
+of the data: negligible for band-limited data, as large as the data for white noise."""
+import numpy as np
+import pytest
+
+from oracle import fbp as F
+from paper_1304_2017_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    from paper_1304_2017_gb300 import oat
+    return torch, oat
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64); b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def smooth_data(geom, seed, width=6.0, n_pulses=3):
+    """Per transducer, a sum of Gaussian pulses (width `width` samples) at seeded delays."""
+    rng = np.random.default_rng(seed)
+    k = np.arange(geom.n_samples)[None, :]
+    p = np.zeros(geom.data_shape)
+    for _ in range(n_pulses):
+        c = rng.uniform(0, geom.n_samples, size=(geom.n_transducers, 1))
+        a = rng.uniform(-1, 1, size=(geom.n_transducers, 1))
+        p += a * np.exp(-0.5 * ((k - c) / width) ** 2)
+    return p.astype(np.float32)
+
+
+def _data(geom, kind, seed):
+    if kind == "smooth":
+        return smooth_data(geom, seed)
+    # the forward model's own data: H of a sphere phantom (the oracle, FP64)
+    import oracle
+    return oracle.H(geom, W.spheres_phantom(geom, 3, seed=seed)).astype(np.float32)
+
+
+CASES = {
+    # non-round sizes: with round ones (0.3 mm, 9 mm, rings at multiples of 30 degrees) many
+    # node-transducer distances land exactly on a sample, where Eq. disfbp switches its
+    # difference pair and the reference's own rounding decides the side
+    "ragged": (lambda: W.make_geometry((13, 10, 11), 0.31, 3, 5, 9.13, 120), "smooth"),
+    "tmin0": (lambda: W.make_geometry(12, 0.29, 2, 4, 6.07, 120, t_min_us=0.0), "smooth"),
+    "window_cut": (lambda: W.make_geometry(14, 0.31, 3, 4, 8.11, 30), "smooth"),
+    "physical": (lambda: W.make_geometry(20, 0.251, 6, 8, 8.03, 160), "forward"),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("dtype", [0, 1, 2])
+def test_fbp_matches_reference(env, case, dtype):
+    torch, oat = env
+    make, kind = CASES[case]
+    geom = make()
+    n_r = {"ragged": 3, "tmin0": 2, "window_cut": 3, "physical": 6}[case]
+    n_v = geom.n_transducers // n_r
+    w = F.arc_weights(geom.positions_mm, n_r, n_v)
+    p = _data(geom, kind, 11)
+    plan = oat.Plan(geom, data_dtype=dtype)
+    plan.set_fbp_weights(w)
+    pt = torch.from_numpy(p).cuda().to(plan.torch_data_dtype)
+    got = plan.fbp(pt).cpu().numpy()
+    want = F.fbp(geom, pt.float().cpu().numpy(), w)
+    assert np.abs(want).max() > 0
+    assert rel(got, want) <= TOL, rel(got, want)
+    plan.close()
+
+
+def test_fbp_full_size_sampled_nodes(env):
+    """256^3, 23,040 transducers, K = 1536: the whole volume on the GPU; 64 sampled nodes
+    (through the grid and its faces) against the reference."""
+    torch, oat = env
+    geom = W.config("c2")
+    w = F.arc_weights(geom.positions_mm, 128, 180)
+    p = smooth_data(geom, seed=41, width=8.0)
+    plan = oat.Plan(geom)
+    plan.set_fbp_weights(w)
+    got = plan.fbp(torch.from_numpy(p).cuda()).cpu().numpy()
+    rng = np.random.default_rng(5)
+    nodes = rng.integers(0, 256, size=(64, 3))
+    nodes[:8, 0] = 0; nodes[8:16, 1] = 255; nodes[16:24, 2] = 0
+    want = F.fbp(geom, p, w, nodes=nodes)
+    got_s = got[nodes[:, 2], nodes[:, 1], nodes[:, 0]]
+    print("fbp full size:", rel(got_s, want))
+    assert rel(got_s, want) <= TOL, rel(got_s, want)
+    plan.close()
+
+
+def test_fbp_requires_weights(env):
+    torch, oat = env
+    geom = W.make_geometry(8, 0.4, 2, 2, 6.0, 32)
+    plan = oat.Plan(geom)
+    d = torch.zeros(geom.data_shape, device="cuda")
+    with pytest.raises(oat.OatError) as e:
+        plan.fbp(d)
+    assert e.value.code == oat.OAT_ERR_INVALID_ARG
+    with pytest.raises(oat.OatError):
+        plan.set_fbp_weights(np.full(geom.n_transducers, np.nan))
+    with pytest.raises(ValueError):
+        plan.set_fbp_weights(np.ones(3))
+    plan.close()
