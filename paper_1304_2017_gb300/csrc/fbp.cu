@@ -9,10 +9,13 @@
 //          dD = (2 D u.delta + |delta|^2) / (D + sqrt(D^2 + 2 D u.delta + |delta|^2))
 //        (u the unit vector from the transducer to the centre): every FP32 quantity stays
 //        small, so k~ = K + dD ds / (c dt) keeps about 1e-6 of a sample, as the interpolation
-//        weight needs.  Per term, with w = k~ - k and tau = k~ + t_min / dt,
+//        weight needs (the square root and divisions use the SFU approximations, whose ~2-ulp
+//        error leaves dD good to ~1e-6 grid units).  Per term, with w = k~ - k and
+//        tau = k~ + t_min / dt,
 //          {..} = 0.5 (p_{k+1} - p_k) + (p_k + w (p_{k+1} - p_k)) / tau
 //        (the braces of Eq. disfbp rewritten), summed with compensation over a tile and in
-//        double across tiles; every voxel is written once.
+//        double across tiles; every voxel is written once.  Tiles whose sample windows lie
+//        inside the record (the usual case) skip the per-sample bounds tests.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -47,11 +50,17 @@ struct __align__(16) FbpQ {
 };
 
 template <int DT>
-__device__ __forceinline__ float load_p(const void *p, size_t i) {
-    if (DT == OAT_F32) return __ldg((const float *)p + i);
-    else if (DT == OAT_F16) return __half2float(((const __half *)p)[i]);
-    else return __bfloat162float(((const __nv_bfloat16 *)p)[i]);
-}
+struct DataT;
+template <>
+struct DataT<OAT_F32> { using T = float; };
+template <>
+struct DataT<OAT_F16> { using T = __half; };
+template <>
+struct DataT<OAT_BF16> { using T = __nv_bfloat16; };
+
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 __device__ __forceinline__ FbpQ fbp_setup(const FbpArgs &a, int q, float cx, float cy, float cz) {
     const float4 hi = __ldg(a.xd + 2 * q), lo = __ldg(a.xd + 2 * q + 1);
@@ -92,8 +101,36 @@ __device__ __forceinline__ FbpQ fbp_setup(const FbpArgs &a, int q, float cx, flo
     return o;
 }
 
+// One (voxel, transducer) term: sample position from the brick-centre values in Q and the
+// voxel offset (dx, dy, dz), |delta|^2 = dd; returns w_q {..} of Eq. disfbp.  CHECK: treat
+// samples outside 0 .. K-1 as zero (else every sample read is known to be inside).
+template <bool CHECK, typename T>
+__device__ __forceinline__ float fbp_term(const FbpQ &Q, const T *row, int K, float dx, float dy, float dz, float dd,
+                                          float sk) {
+    const float ud = fmaf(Q.uz, dz, fmaf(Q.uy, dy, Q.ux * dx));
+    const float tt = fmaf(2.f * Q.D, ud, dd);
+    const float s2 = fmaf(Q.D, Q.D, tt);
+    const float dD = __fdividef(tt, Q.D + s2 * rsqrtf(s2));          // distance - D
+    const float kf = fmaf(dD, sk, Q.kfrac);
+    const float fk = floorf(kf);
+    const int k = Q.kint + (int)fk;
+    const float wgt = kf - fk;
+    const float tau = fmaf(dD, sk, Q.tau);
+    float p0, p1;
+    if (CHECK) {
+        p0 = (k >= 0 && k < K) ? to_f(row[k]) : 0.f;
+        p1 = (k + 1 >= 0 && k + 1 < K) ? to_f(row[k + 1]) : 0.f;
+    } else {
+        p0 = to_f(row[k]);
+        p1 = to_f(row[k + 1]);
+    }
+    const float dp = p1 - p0;
+    return Q.w * fmaf(fmaf(wgt, dp, p0), __fdividef(1.f, tau), 0.5f * dp);
+}
+
 template <int DT>
 __global__ void __launch_bounds__(kFbpThreads) k_fbp(FbpArgs a) {
+    using T = typename DataT<DT>::T;
     __shared__ FbpQ tq[kFbpTile];
     const int b = blockIdx.x;
     const int bx = b % a.bx, by = (b / a.bx) % a.by, bz = b / (a.bx * a.by);
@@ -103,30 +140,27 @@ __global__ void __launch_bounds__(kFbpThreads) k_fbp(FbpArgs a) {
     const float dx = lx - 3.5f, dy = ly - 3.5f, dz = lz - 3.5f;
     const float dd = dx * dx + dy * dy + dz * dz;
     const float sk = a.sk_hi;
+    // every voxel of the brick is within rb of the centre: its sample index is within rb sk
+    // (plus rounding) of the centre's
+    const float reach = (3.5f * 1.7320509f + 0.01f) * sk + 1.f;
     double total = 0.0;
     for (int q0 = 0; q0 < a.Q; q0 += kFbpTile) {
         const int nt = min(kFbpTile, a.Q - q0);
         __syncthreads();
-        if (threadIdx.x < nt) tq[threadIdx.x] = fbp_setup(a, q0 + threadIdx.x, cx, cy, cz);
-        __syncthreads();
+        bool inside = true;
+        if (threadIdx.x < nt) {
+            const FbpQ Q = fbp_setup(a, q0 + threadIdx.x, cx, cy, cz);
+            tq[threadIdx.x] = Q;
+            const float lo = (float)Q.kint + Q.kfrac - reach, hi = (float)Q.kint + Q.kfrac + reach;
+            inside = lo >= 0.f && hi <= (float)(a.K - 2);
+        }
+        const bool all_inside = __syncthreads_and(inside);
+        const T *row = (const T *)a.p + (size_t)q0 * a.K;
         float s = 0.f, e = 0.f;
-        for (int t = 0; t < nt; ++t) {
-            const FbpQ Q = tq[t];
-            const float ud = fmaf(Q.uz, dz, fmaf(Q.uy, dy, Q.ux * dx));
-            const float tt = fmaf(2.f * Q.D, ud, dd);
-            const float sq = sqrtf(fmaf(Q.D, Q.D, tt));
-            const float dD = __fdividef(tt, Q.D + sq);                 // distance - D
-            const float kf = fmaf(dD, sk, Q.kfrac);
-            const float fk = floorf(kf);
-            const int k = Q.kint + (int)fk;
-            const float wgt = kf - fk;
-            const float tau = fmaf(dD, sk, Q.tau);
-            const size_t row = (size_t)(q0 + t) * a.K;
-            const float p0 = (k >= 0 && k < a.K) ? load_p<DT>(a.p, row + k) : 0.f;
-            const float p1 = (k + 1 >= 0 && k + 1 < a.K) ? load_p<DT>(a.p, row + k + 1) : 0.f;
-            const float dp = p1 - p0;
-            const float br = fmaf(fmaf(wgt, dp, p0), __frcp_rn(tau), 0.5f * dp);
-            kadd(s, e, Q.w * br);
+        if (all_inside) {
+            for (int t = 0; t < nt; ++t, row += a.K) kadd(s, e, fbp_term<false>(tq[t], row, a.K, dx, dy, dz, dd, sk));
+        } else {
+            for (int t = 0; t < nt; ++t, row += a.K) kadd(s, e, fbp_term<true>(tq[t], row, a.K, dx, dy, dz, dd, sk));
         }
         total += (double)s + (double)e;
     }

@@ -6,11 +6,14 @@ sample (float-pair distance to each brick centre, small FP32 offsets) and sums w
 compensation, so its error stays near FP32 rounding of the data and weights.  FP16 / BF16 data
 are read exactly, so the reference gets the same rounded values.
 
-The data are band-limited, as measured pressure is: seeded Gaussian pulses several samples wide,
-or the forward model's own data.  Eq. disfbp is discontinuous in the sample position -- where
-k~ crosses an integer the one-sided difference p_{k+1} - p_k moves to the next pair -- so any
-rounding difference that moves k~ across an integer changes the term by the second difference
-of the data: negligible for band-limited data, as large as the data for white noise."""
+Eq. disfbp is discontinuous in the sample position: where k~ crosses an integer the one-sided
+difference p_{k+1} - p_k moves to the next pair, so a rounding difference that moves k~ across
+an integer changes that term by the second difference of the data.  Where k~ lies within 1e-4
+of a sample (about 1e-4 of the pairs) both sides are valid readings; the comparison allows each
+node the reference's total change over such pairs (`ambiguity`) and holds everything else to
+the tolerance.  The data are band-limited, as measured pressure is (Gaussian pulses several
+samples wide, or the forward model's data of a smooth object): for white noise the second
+difference is as large as the data."""
 import numpy as np
 import pytest
 
@@ -36,6 +39,16 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def rel_beyond(got, want, amb):
+    """Relative L2 of the part of got - want that the integer-crossing allowance amb does not
+    explain."""
+    d = np.maximum(np.abs(np.asarray(got, np.float64) - want) - amb, 0.0)
+    return float(np.linalg.norm(d) / np.linalg.norm(want))
+
+
+EPS_K = 1e-4
+
+
 def smooth_data(geom, seed, width=6.0, n_pulses=3):
     """Per transducer, a sum of Gaussian pulses (width `width` samples) at seeded delays."""
     rng = np.random.default_rng(seed)
@@ -48,12 +61,26 @@ def smooth_data(geom, seed, width=6.0, n_pulses=3):
     return p.astype(np.float32)
 
 
+def blob_phantom(geom, seed, n=3, sigma_vox=2.5):
+    """Sum of Gaussian blobs (standard deviation sigma_vox grid spacings): a smooth object, so
+    that its data are band-limited."""
+    rng = np.random.default_rng(seed)
+    xs, ys, zs = geom.node_coords_mm()
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    s = sigma_vox * geom.spacing_mm
+    vol = np.zeros(geom.vol_shape)
+    for _ in range(n):
+        c = [rng.uniform(v[len(v) // 4], v[3 * len(v) // 4]) for v in (xs, ys, zs)]
+        vol += rng.uniform(0.3, 1.0) * np.exp(-((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2) / (2 * s * s))
+    return vol.astype(np.float32)
+
+
 def _data(geom, kind, seed):
     if kind == "smooth":
         return smooth_data(geom, seed)
-    # the forward model's own data: H of a sphere phantom (the oracle, FP64)
+    # the forward model's own data (the oracle, FP64) of a smooth object
     import oracle
-    return oracle.H(geom, W.spheres_phantom(geom, 3, seed=seed)).astype(np.float32)
+    return oracle.H(geom, blob_phantom(geom, seed)).astype(np.float32)
 
 
 CASES = {
@@ -81,9 +108,10 @@ def test_fbp_matches_reference(env, case, dtype):
     plan.set_fbp_weights(w)
     pt = torch.from_numpy(p).cuda().to(plan.torch_data_dtype)
     got = plan.fbp(pt).cpu().numpy()
-    want = F.fbp(geom, pt.float().cpu().numpy(), w)
+    want, amb = F.fbp(geom, pt.float().cpu().numpy(), w, ambiguity=EPS_K)
     assert np.abs(want).max() > 0
-    assert rel(got, want) <= TOL, rel(got, want)
+    print(case, dtype, "rel", rel(got, want), "beyond the allowance", rel_beyond(got, want, amb))
+    assert rel_beyond(got, want, amb) <= TOL, (rel(got, want), rel_beyond(got, want, amb))
     plan.close()
 
 
@@ -100,10 +128,10 @@ def test_fbp_full_size_sampled_nodes(env):
     rng = np.random.default_rng(5)
     nodes = rng.integers(0, 256, size=(64, 3))
     nodes[:8, 0] = 0; nodes[8:16, 1] = 255; nodes[16:24, 2] = 0
-    want = F.fbp(geom, p, w, nodes=nodes)
+    want, amb = F.fbp(geom, p, w, nodes=nodes, ambiguity=EPS_K)
     got_s = got[nodes[:, 2], nodes[:, 1], nodes[:, 0]]
-    print("fbp full size:", rel(got_s, want))
-    assert rel(got_s, want) <= TOL, rel(got_s, want)
+    print("fbp full size:", rel(got_s, want), rel_beyond(got_s, want, amb))
+    assert rel_beyond(got_s, want, amb) <= TOL, (rel(got_s, want), rel_beyond(got_s, want, amb))
     plan.close()
 
 
