@@ -254,16 +254,19 @@ def run_pls(args):
 
 
 def run_fbp(args):
-    """Filtered backprojection (Eq. disfbp) on the 256^3 / 23,040-transducer / K = 1536 workload:
-    seconds per reconstruction and voxel-transducer pairs per second, CUDA events around W
-    untimed and K timed calls; the FP64 reference timed on a 16-transducer sample."""
+    """Filtered backprojection (Eq. disfbp) on a workload (default the 256^3 / 23,040-transducer /
+    K = 1536 one): seconds per reconstruction and voxel-transducer pairs per second, CUDA events
+    around W untimed and K timed calls; the FP64 reference timed on a 16-transducer sample."""
     import torch
     from paper_1304_2017_gb300 import oat
     from paper_1304_2017_gb300 import workloads as W
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     geom = W.config(args.config)
-    n_r, n_v = (128, 180) if args.config == "c2" else (None, None)
+    scans = {"c1": (16, 16), "c2": (128, 180), "c3": (96, 90), "c5": (128, 60)}
+    if args.config not in scans:
+        raise SystemExit(f"--fbp: no rings x views scan known for --config {args.config}")
+    n_r, n_v = scans[args.config]
     pos = geom.positions_mm
     rs = np.linalg.norm(pos, axis=1)
     theta = np.arccos(np.clip(pos[:, 2] / rs, -1.0, 1.0))
@@ -286,7 +289,7 @@ def run_fbp(args):
     line = {"metric": "FBP voxel-transducer pairs/s (filtered backprojection, Eq. disfbp)", "value": pairs / sec,
             "unit": "pairs/s", "seconds_per_fbp": sec, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "pairs": pairs}}
+            "config": {"workload": W.DESCRIPTIONS.get(args.config, args.config), "pairs": pairs}}
     if not args.no_cpu_baseline:
         import oracle.fbp as F
         qs = np.linspace(0, geom.n_transducers - 1, 16).round().astype(int)
