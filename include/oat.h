@@ -168,6 +168,28 @@ int oat_plan_set_fbp_weights(oat_plan plan, const double *weights);
 int oat_fbp(oat_plan plan, const void *d_data, float *d_vol, void *stream);
 
 /*
+ * Transducer response (Sec. II.B, Eq. EIR): the full model H = H^e D G, with
+ *   [H^e p]_{q,k} = sum_{kappa=0}^{K-1} h_{k-1-kappa} p_{q,kappa},
+ *   h_m = dt h^e(m dt) for m = first_index .. first_index + n_taps - 1, zero elsewhere,
+ * and its adjoint H^T = G^T D^T H^e^T with [H^e^T u]_{q,k} = sum_kappa h_{kappa-1-k} u_{q,kappa}
+ * (sums over the record 0 .. K-1 only).  Once set, oat_project returns H^e D G alpha (D G alpha
+ * kept in double precision in shared memory, the convolution in double, one rounding to the data
+ * dtype) and oat_backproject / oat_backproject_noalloc compute z = H^e^T y in double from the
+ * stored y, rounded once to float32 into a plan-owned [Q][K] buffer that the voxel gather reads.
+ *
+ * oat_plan_set_eir: h host array of n_taps doubles (copied; synchronous); n_taps = 0 removes the
+ *   response (h may then be NULL).  The first call allocates the float32 [Q][K] buffer
+ *   (Q K 4 bytes, counted in oat_stats.scratch_bytes), kept until oat_plan_destroy; later calls
+ *   allocate only the tap array.  Calls must not overlap with the plan's work in flight.
+ *   With a response set, oat_backproject / oat_backproject_noalloc on one plan share that
+ *   buffer: order them (one stream).
+ * Errors: OAT_ERR_INVALID_ARG (NULL plan, n_taps < 0, NULL h with n_taps > 0, non-finite tap,
+ *         |first_index| > 2^30, (n_samples + n_taps) doubles above a block's shared memory),
+ *         OAT_ERR_OOM, OAT_ERR_CUDA.
+ */
+int oat_plan_set_eir(oat_plan plan, const double *h, int n_taps, int first_index);
+
+/*
  * Fill *stats.  With count_grid_points != 0 the call also counts, on the device and
  * synchronously (on the legacy default stream), the lattice points whose interpolation
  * stencil touches the grid, the unit of work of the throughput metric.

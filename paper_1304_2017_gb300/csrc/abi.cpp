@@ -121,6 +121,50 @@ int oat_fbp(oat_plan plan, const void *d_data, float *d_vol, void *stream) {
     return launch_fbp(*p, d_data, d_vol, (cudaStream_t)stream);
 }
 
+int oat_plan_set_eir(oat_plan plan, const double *h, int n_taps, int first_index) {
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p) return set_error(OAT_ERR_INVALID_ARG, "oat_plan_set_eir: NULL plan");
+    if (n_taps < 0 || (n_taps > 0 && !h)) return set_error(OAT_ERR_INVALID_ARG, "oat_plan_set_eir: bad tap array");
+    for (int i = 0; i < n_taps; ++i)
+        if (!std::isfinite(h[i])) return set_error(OAT_ERR_INVALID_ARG, "oat_plan_set_eir: non-finite tap");
+    if (first_index < -(1 << 30) || first_index > (1 << 30))
+        return set_error(OAT_ERR_INVALID_ARG, "oat_plan_set_eir: first_index out of range (|m0| <= 2^30)");
+    DeviceGuard dg(p->device);
+    if (dg.err != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_plan_set_eir: ") + cudaGetErrorString(dg.err));
+    if (n_taps == 0) {
+        p->eir_n = 0;
+        return OAT_OK;
+    }
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    if (sizeof(double) * ((size_t)p->K + (size_t)n_taps) > (size_t)optin)
+        return set_error(OAT_ERR_INVALID_ARG, "oat_plan_set_eir: n_samples + n_taps doubles exceed the shared memory of a block");
+    cudaError_t e = cudaSuccess;
+    if (!p->d_eir_z) {
+        e = cudaMalloc(&p->d_eir_z, sizeof(float) * (size_t)p->Q * p->K);
+        if (e != cudaSuccess) {
+            p->d_eir_z = nullptr;
+            cudaGetLastError();
+            return set_error(e == cudaErrorMemoryAllocation ? OAT_ERR_OOM : OAT_ERR_CUDA,
+                             std::string("oat_plan_set_eir: cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        p->scratch_bytes += (long long)(sizeof(float) * (size_t)p->Q * p->K);
+    }
+    if (p->d_eir) { cudaFree(p->d_eir); p->d_eir = nullptr; }
+    e = cudaMalloc(&p->d_eir, sizeof(double) * (size_t)n_taps);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_eir, h, sizeof(double) * (size_t)n_taps, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (p->d_eir) { cudaFree(p->d_eir); p->d_eir = nullptr; }
+        p->eir_n = 0;
+        cudaGetLastError();
+        return set_error(e == cudaErrorMemoryAllocation ? OAT_ERR_OOM : OAT_ERR_CUDA,
+                         std::string("oat_plan_set_eir: ") + cudaGetErrorString(e));
+    }
+    p->eir_n = n_taps;
+    p->eir_m0 = first_index;
+    return set_eir_attributes(*p);
+}
+
 int oat_plan_query(oat_plan plan, int want_count, oat_stats *st) {
     Plan *p = reinterpret_cast<Plan *>(plan);
     if (!p || !st) return set_error(OAT_ERR_INVALID_ARG, "oat_plan_query: NULL plan or stats");

@@ -261,7 +261,15 @@ static int backproject_with(Plan &p, const void *data, float *vol, cudaStream_t 
     cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(unsigned int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(vacc, 0, sizeof(long long) * N, s);
     if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_backproject: memset: ") + cudaGetErrorString(e));
-    k_absmax<<<(unsigned)std::min<size_t>((M + 255) / 256, 152 * 8), 256, 0, s>>>(data, M, p.g.data_dtype, amax);
+    // with a transducer response the gather reads z = H^e^T y (float32) instead of y
+    int dtype = p.g.data_dtype;
+    if (p.eir_n > 0) {
+        const int rc = launch_eir_t(p, data, p.d_eir_z, s);
+        if (rc != OAT_OK) return rc;
+        data = p.d_eir_z;
+        dtype = OAT_F32;
+    }
+    k_absmax<<<(unsigned)std::min<size_t>((M + 255) / 256, 152 * 8), 256, 0, s>>>(data, M, dtype, amax);
     AdjArgs a;
     a.t = p.t; a.y = data;
     a.vacc = (unsigned long long *)vacc;
@@ -275,7 +283,7 @@ static int backproject_with(Plan &p, const void *data, float *vol, cudaStream_t 
     const bool prof = p.profiling && p.ev_used[1] + 2 <= (int)p.ev[1].size();
     if (prof) cudaEventRecord(p.ev[1][p.ev_used[1]], s);
     const unsigned grid = (unsigned)p.adj.items;
-    switch (p.g.data_dtype) {
+    switch (dtype) {
         case OAT_F32: k_brick_gather_t<kBA, OAT_F32><<<grid, kAdjThreads, p.adj.smem, s>>>(a); break;
         case OAT_F16: k_brick_gather_t<kBA, OAT_F16><<<grid, kAdjThreads, p.adj.smem, s>>>(a); break;
         default: k_brick_gather_t<kBA, OAT_BF16><<<grid, kAdjThreads, p.adj.smem, s>>>(a); break;

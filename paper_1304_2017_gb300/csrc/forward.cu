@@ -254,6 +254,7 @@ int launch_project(Plan &p, const float *vol, void *data, cudaStream_t s) {
     if (prof) { cudaEventRecord(p.ev[0][p.ev_used[0] + 1], s); p.ev_used[0] += 2; }
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_project: k_brick_gather: ") + cudaGetErrorString(e));
+    if (p.eir_n > 0) return launch_apply_d_eir(p, data, s);
     const size_t n = (size_t)p.Q * p.K;
     const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
     const int dt = p.g.data_dtype;

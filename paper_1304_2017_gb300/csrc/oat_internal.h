@@ -113,6 +113,12 @@ struct Plan {
     float4 *d_fbp = nullptr;
     std::vector<float4> fbp_host;
     bool fbp_weights = false;
+
+    // transducer response H^e: taps h_m for m = eir_m0 .. eir_m0 + eir_n - 1 (none when
+    // eir_n == 0) and the float32 [Q][K] buffer that holds H^e^T y for the backprojector
+    double *d_eir = nullptr;
+    float *d_eir_z = nullptr;
+    int eir_n = 0, eir_m0 = 0;
 };
 
 // status helpers (abi.cpp)
@@ -123,6 +129,12 @@ int launch_project(Plan &p, const float *vol, void *data, cudaStream_t s);
 int launch_backproject(Plan &p, const void *data, float *vol, cudaStream_t s);
 int launch_backproject_static(Plan &p, const void *data, float *vol, cudaStream_t s);
 int count_grid_points(Plan &p, long long *out);
+
+// transducer response (eir.cu)
+size_t eir_smem_bytes(const Plan &p);
+int set_eir_attributes(const Plan &p);
+int launch_apply_d_eir(Plan &p, void *data, cudaStream_t s);
+int launch_eir_t(Plan &p, const void *y, float *z, cudaStream_t s);
 int launch_fbp(Plan &p, const void *data, float *vol, cudaStream_t s);
 int set_adjoint_attributes();
 int set_forward_attributes();

@@ -340,6 +340,8 @@ void plan_destroy(Plan *p) {
     if (p->d_gacc) cudaFree(p->d_gacc);
     if (p->d_vacc) cudaFree(p->d_vacc);
     if (p->d_amax) cudaFree(p->d_amax);
+    if (p->d_eir) cudaFree(p->d_eir);
+    if (p->d_eir_z) cudaFree(p->d_eir_z);
     cudaSetDevice(prev);
     delete p;
 }

@@ -58,6 +58,7 @@ def _load():
     lib.oat_backproject_noalloc.argtypes = [vp, vp, vp, vp]
     lib.oat_plan_set_fbp_weights.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     lib.oat_fbp.argtypes = [vp, vp, vp, vp]
+    lib.oat_plan_set_eir.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int]
     lib.oat_plan_query.argtypes = [vp, ctypes.c_int, ctypes.POINTER(oat_stats)]
     lib.oat_plan_set_profiling.argtypes = [vp, ctypes.c_int]
     lib.oat_plan_kernel_time.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -75,7 +76,7 @@ def _load():
     lib.oat_last_error.restype = ctypes.c_char_p
     lib.oat_version.restype = ctypes.c_int
     for name in ("oat_plan_create", "oat_plan_destroy", "oat_project", "oat_backproject", "oat_backproject_noalloc",
-                 "oat_plan_query", "oat_plan_set_fbp_weights", "oat_fbp",
+                 "oat_plan_query", "oat_plan_set_fbp_weights", "oat_fbp", "oat_plan_set_eir",
                  "oat_plan_set_profiling", "oat_plan_kernel_time"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
@@ -136,6 +137,12 @@ def oat_backproject_noalloc(handle, d_data, d_vol, stream=0):
 def oat_plan_set_fbp_weights(handle, weights):
     w = np.ascontiguousarray(weights, dtype=np.float64)
     return _check(lib.oat_plan_set_fbp_weights(handle, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+
+def oat_plan_set_eir(handle, h, first_index=0):
+    t = np.ascontiguousarray(h, dtype=np.float64).reshape(-1)
+    ptr = t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if t.size else None
+    return _check(lib.oat_plan_set_eir(handle, ptr, int(t.size), int(first_index)))
 
 
 def oat_fbp(handle, d_data, d_vol, stream=0):
@@ -258,6 +265,11 @@ class Plan:
         if w.shape != (self.data_shape[0],):
             raise ValueError(f"weights: expected {self.data_shape[0]} values, got shape {w.shape}")
         oat_plan_set_fbp_weights(self.handle, w)
+
+    def set_eir(self, h, first_index=0):
+        """Transducer response taps h_m for m = first_index, first_index + 1, ... (Eq. EIR); from
+        then on project is H^e D G and backproject its adjoint.  An empty h removes it."""
+        oat_plan_set_eir(self.handle, h, first_index)
 
     def fbp(self, data, out=None):
         """Filtered backprojection of data [Q][K] (plan's data dtype) -> (nz, ny, nx) float32."""

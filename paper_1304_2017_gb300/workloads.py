@@ -218,6 +218,31 @@ def random_volume(geom: Geometry, seed=11, dtype=np.float32):
     return rng.standard_normal(geom.vol_shape).astype(dtype)
 
 
+def eir_taps(fs_mhz=20.0, kind="gaussian", fwhm_us=0.5, centre_mhz=2.25, cycles=1.5):
+    """Synthetic transducer-response taps h_m = dt h^e(m dt) and their first index m0.
+
+    kind="gaussian": the temporal blur of the simulation studies (a Gaussian of FWHM `fwhm_us`,
+    unit area), centred (no delay: its peak at m = -1, where the model's one-sample offset
+    cancels).  kind="bandpass": a causal band-pass pulse, a Gaussian-windowed cosine of centre
+    frequency `centre_mhz` with `cycles` cycles per standard deviation, zero mean, starting at
+    m = 0 (a stand-in for a measured EIR)."""
+    dt = 1.0 / fs_mhz
+    if kind == "gaussian":
+        sig = fwhm_us / (2.0 * np.sqrt(2.0 * np.log(2.0))) / dt       # samples
+        half = int(np.ceil(4.0 * sig))
+        m = np.arange(-half, half + 1)
+        h = np.exp(-0.5 * (m / sig) ** 2)
+        return h / h.sum(), -1 - half
+    if kind == "bandpass":
+        sig = cycles / centre_mhz / dt
+        n = int(np.ceil(8.0 * sig)) + 1
+        t = np.arange(n) - 4.0 * sig
+        h = np.exp(-0.5 * (t / sig) ** 2) * np.cos(2.0 * np.pi * centre_mhz * dt * t)
+        h -= h.mean() * np.exp(-0.5 * (t / sig) ** 2) / np.exp(-0.5 * (t / sig) ** 2).mean()
+        return dt * h / np.abs(dt * h).sum(), 0
+    raise ValueError(kind)
+
+
 # ----------------------------------------------------------------------------- configurations
 
 def _c1():
