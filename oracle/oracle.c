@@ -27,6 +27,10 @@
  *   - D uses tau_k = t_min/dt + k; rows 0 and K-1 are zero; a term with tau <= 0 is zero
  *                                                                                 (Eq. dis_g2p)
  *   - D^T is the exact transpose of that D (masked neighbours), not the paper's printed loop.
+ *   - point weights (Eq. dis_srt): ds^2 for every point (area = 0), or, with area = 1, the
+ *     area of ring i's strip of the shell shared by its points, ds * 2 pi rho sin(theta_i) / N_j
+ *     (the strip has polar width dtheta, i.e. ds on the shell, and circumference
+ *     2 pi rho sin(theta_i)); the latter removes the bias of rounding 2 pi / dphi_i down to N_j.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -47,6 +51,7 @@ typedef struct {
     double c;           /* speed of sound (mm/us) */
     double R;           /* support radius (mm) */
     double gamma;       /* Grueneisen coefficient Gamma = beta c^2 / C_p */
+    int area;           /* 0: weight ds^2 per lattice point; 1: exact strip area per point */
 } orc_geom;
 
 /* ------------------------------------------------------------------ geometry (Appendix) */
@@ -91,6 +96,14 @@ static int ring_points(const orc_geom *g, double rho, double th, double *dph_out
     double dph = g->ds / (rho * st);   /* +inf at the pole: no points */
     *dph_out = dph;
     return (int)floor(2.0 * M_PI / dph);
+}
+
+/* Weight of each point of ring i relative to ds^2: 1, or with exact strip areas
+ * (ds * 2 pi rho sin(theta_i) / N_j) / ds^2. */
+static double ring_weight(const orc_geom *g, double rho, double th, int nj)
+{
+    if (!g->area || nj <= 0) return 1.0;
+    return 2.0 * M_PI * rho * sin(th) / (nj * g->ds);
 }
 
 /* Global position (mm) of lattice point (k, i, j) of transducer q  (r_{k,i,j}, Appendix). */
@@ -163,7 +176,8 @@ static void splat(const orc_geom *g, double *out, const double P[3], double v)
 
 /* ------------------------------------------------------------------ G (Eq. dis_srt) */
 
-/* One data sample: g_{qK+k} = ds^2 * sum_{i<N_i} sum_{j<N_j} f(r_{k,i,j}). */
+/* One data sample: g_{qK+k} = ds^2 * sum_{i<N_i} w_i sum_{j<N_j} f(r_{k,i,j}) (w_i = 1 unless
+ * exact strip areas are asked for). */
 static double G_sample(const orc_geom *g, const double *alpha, int q, int k)
 {
     double ex[3], ey[3], ez[3], rs, rho, dth, dph;
@@ -174,11 +188,13 @@ static double G_sample(const orc_geom *g, const double *alpha, int q, int k)
     for (int i = 0; i < ni; ++i) {
         double th = i * dth;
         int nj = ring_points(g, rho, th, &dph);
+        double wi = ring_weight(g, rho, th, nj), si = 0.0;
         for (int j = 0; j < nj; ++j) {
             double P[3];
             lattice_point(rq, ex, ey, ez, rho, th, j * dph, P);
-            s += interp(g, alpha, P);
+            si += interp(g, alpha, P);
         }
+        s += wi * si;
     }
     return g->ds * g->ds * s;
 }
@@ -214,10 +230,11 @@ static void Gt_transducer(const orc_geom *g, const double *gp, int q, double *ou
         for (int i = 0; i < ni; ++i) {
             double th = i * dth;
             int nj = ring_points(g, rho, th, &dph);
+            double vi = v * ring_weight(g, rho, th, nj);
             for (int j = 0; j < nj; ++j) {
                 double P[3];
                 lattice_point(rq, ex, ey, ez, rho, th, j * dph, P);
-                splat(g, out, P, v);
+                splat(g, out, P, vi);
             }
         }
     }
@@ -282,6 +299,7 @@ void oracle_Gt_nodes(const orc_geom *g, const double *gp, const int *nodes, int 
                     double th = i * dth;
                     if (fabs(th - thn) > amax + 1e-9) continue;
                     int nj = ring_points(g, rho, th, &dph);
+                    double si = 0.0;
                     for (int j = 0; j < nj; ++j) {
                         double P[3];
                         lattice_point(rq, ex, ey, ez, rho, th, j * dph, P);
@@ -290,8 +308,9 @@ void oracle_Gt_nodes(const orc_geom *g, const double *gp, const int *nodes, int 
                             double u = fabs(P[dd] - rn[dd]) / g->ds;
                             t *= (u < 1.0) ? 1.0 - u : 0.0;
                         }
-                        ss += t;
+                        si += t;
                     }
+                    ss += ring_weight(g, rho, th, nj) * si;
                 }
                 s += w * ss;
             }
@@ -366,7 +385,7 @@ void oracle_Ht(const orc_geom *g, const double *y, double *out, int apply_d)
 
 /* ------------------------------------------------------------------ brute force and inspection */
 
-/* Dense G: M[(q*K + k)*N + n] = ds^2 sum_{i,j} psi_n(r_{k,i,j}), with psi_n evaluated from its
+/* Dense G: M[(q*K + k)*N + n] = ds^2 sum_{i,j} w_i psi_n(r_{k,i,j}), with psi_n evaluated from its
  * definition for every node n (no 8-neighbour shortcut).  Tiny grids only. */
 void oracle_dense_G(const orc_geom *g, double *M)
 {
@@ -382,6 +401,7 @@ void oracle_dense_G(const orc_geom *g, double *M)
             for (int i = 0; i < ni; ++i) {
                 double th = i * dth;
                 int nj = ring_points(g, rho, th, &dph);
+                double wi = ring_weight(g, rho, th, nj);
                 for (int j = 0; j < nj; ++j) {
                     double P[3];
                     lattice_point(rq, ex, ey, ez, rho, th, j * dph, P);
@@ -394,7 +414,7 @@ void oracle_dense_G(const orc_geom *g, double *M)
                                 double ax = fabs(P[0] - xn), ay = fabs(P[1] - yn), az = fabs(P[2] - zn);
                                 if (ax <= g->ds && ay <= g->ds && az <= g->ds)
                                     row[((long)iz * g->ny + iy) * g->nx + ix] +=
-                                        g->ds * g->ds * (1.0 - ax / g->ds) * (1.0 - ay / g->ds) * (1.0 - az / g->ds);
+                                        wi * g->ds * g->ds * (1.0 - ax / g->ds) * (1.0 - ay / g->ds) * (1.0 - az / g->ds);
                             }
                 }
             }
@@ -403,8 +423,8 @@ void oracle_dense_G(const orc_geom *g, double *M)
 }
 
 /* Rings and points of one shell: returns the number of points; writes at most cap points
- * (mm, [n][3]) and their (i, j) indices. */
-long oracle_shell_points(const orc_geom *g, int q, int k, double *P, int *ij, long cap, int *n_rings)
+ * (mm, [n][3]), their (i, j) indices and their weights (mm^2). */
+long oracle_shell_points(const orc_geom *g, int q, int k, double *P, int *ij, double *wts, long cap, int *n_rings)
 {
     double ex[3], ey[3], ez[3], rs, rho, dth, dph;
     const double *rq = g->pos + 3 * q;
@@ -415,10 +435,12 @@ long oracle_shell_points(const orc_geom *g, int q, int k, double *P, int *ij, lo
     for (int i = 0; i < ni; ++i) {
         double th = i * dth;
         int nj = ring_points(g, rho, th, &dph);
+        double wi = ring_weight(g, rho, th, nj) * g->ds * g->ds;
         for (int j = 0; j < nj; ++j, ++n) {
             if (n < cap) {
                 if (P) lattice_point(rq, ex, ey, ez, rho, th, j * dph, P + 3 * n);
                 if (ij) { ij[2 * n] = i; ij[2 * n + 1] = j; }
+                if (wts) wts[n] = wi;
             }
         }
     }

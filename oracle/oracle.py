@@ -31,7 +31,8 @@ class _Geom(ctypes.Structure):
                 ("ds", ctypes.c_double), ("origin", ctypes.c_double * 3),
                 ("nq", ctypes.c_int), ("pos", ctypes.POINTER(ctypes.c_double)),
                 ("nk", ctypes.c_int), ("fs", ctypes.c_double), ("tmin", ctypes.c_double),
-                ("c", ctypes.c_double), ("R", ctypes.c_double), ("gamma", ctypes.c_double)]
+                ("c", ctypes.c_double), ("R", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("area", ctypes.c_int)]
 
 
 _lib = None
@@ -53,7 +54,7 @@ def _L():
         _lib.oracle_H.argtypes = [gp, dp, dp, ctypes.c_int]
         _lib.oracle_Ht.argtypes = [gp, dp, dp, ctypes.c_int]
         _lib.oracle_dense_G.argtypes = [gp, dp]
-        _lib.oracle_shell_points.argtypes = [gp, ctypes.c_int, ctypes.c_int, dp, ip, ctypes.c_long, ip]
+        _lib.oracle_shell_points.argtypes = [gp, ctypes.c_int, ctypes.c_int, dp, ip, dp, ctypes.c_long, ip]
         _lib.oracle_shell_points.restype = ctypes.c_long
         _lib.oracle_count_points.argtypes = [gp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
         _lib.oracle_max_threads.restype = ctypes.c_int
@@ -76,7 +77,8 @@ class _G:
         self.pos = np.ascontiguousarray(geom.positions_mm, dtype=np.float64)
         self.s = _Geom(geom.nx, geom.ny, geom.nz, geom.spacing_mm, (ctypes.c_double * 3)(*geom.origin_mm),
                        self.pos.shape[0], _dp(self.pos), geom.n_samples, geom.fs_mhz, geom.t_min_us,
-                       geom.c_mm_per_us, geom.support_radius_mm, geom.gruneisen)
+                       geom.c_mm_per_us, geom.support_radius_mm, geom.gruneisen,
+                       int(getattr(geom, "lattice_weights", 0)))
         self.ref = ctypes.byref(self.s)
 
 
@@ -179,15 +181,17 @@ def dense_G(geom):
     return M
 
 
-def shell_points(geom, q, k):
-    """(points [n, 3] in mm, ij [n, 2], number of rings) of the shell of sample (q, k)."""
+def shell_points(geom, q, k, with_weights=False):
+    """(points [n, 3] in mm, ij [n, 2], number of rings) of the shell of sample (q, k); with
+    with_weights also the points' weights (mm^2) as a fourth element."""
     g = _G(geom)
     nr = ctypes.c_int(0)
-    n = _L().oracle_shell_points(g.ref, q, k, None, None, 0, ctypes.byref(nr))
+    n = _L().oracle_shell_points(g.ref, q, k, None, None, None, 0, ctypes.byref(nr))
     P = np.empty((max(n, 1), 3))
     ij = np.empty((max(n, 1), 2), dtype=np.int32)
-    _L().oracle_shell_points(g.ref, q, k, _dp(P), _ip(ij), n, ctypes.byref(nr))
-    return P[:n], ij[:n], nr.value
+    w = np.empty(max(n, 1))
+    _L().oracle_shell_points(g.ref, q, k, _dp(P), _ip(ij), _dp(w), n, ctypes.byref(nr))
+    return (P[:n], ij[:n], nr.value, w[:n]) if with_weights else (P[:n], ij[:n], nr.value)
 
 
 def count_points(geom):

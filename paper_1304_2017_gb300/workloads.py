@@ -39,6 +39,7 @@ class Geometry:
     c_mm_per_us: float          # speed of sound
     support_radius_mm: float    # R: sphere (centred at the origin) that contains the object
     gruneisen: float = 1.0      # Gamma = beta c^2 / C_p, scales D
+    lattice_weights: int = 0    # 0: Delta_s^2 per shell-lattice point; 1: exact ring-strip area
 
     @property
     def n_transducers(self) -> int:
@@ -110,7 +111,7 @@ def centred_tmin(radius_mm, n_samples, fs_mhz, c):
 
 def make_geometry(n, spacing_mm, rings, views, radius_mm, n_samples, fs_mhz=20.0, c=1.5,
                   t_min_us=None, support_radius_mm=None, gruneisen=1.0, theta_min=None,
-                  positions_mm=None, origin_mm=None):
+                  positions_mm=None, origin_mm=None, lattice_weights=0):
     nx, ny, nz = (n, n, n) if np.isscalar(n) else tuple(n)
     origin = centred_origin(nx, ny, nz, spacing_mm) if origin_mm is None else tuple(origin_mm)
     pos = arc_positions(rings, views, radius_mm, theta_min) if positions_mm is None else \
@@ -120,7 +121,7 @@ def make_geometry(n, spacing_mm, rings, views, radius_mm, n_samples, fs_mhz=20.0
     if t_min_us is None:
         t_min_us = centred_tmin(radius_mm, n_samples, fs_mhz, c)
     return Geometry(nx, ny, nz, float(spacing_mm), origin, pos, int(n_samples), float(fs_mhz),
-                    float(t_min_us), float(c), float(support_radius_mm), float(gruneisen))
+                    float(t_min_us), float(c), float(support_radius_mm), float(gruneisen), int(lattice_weights))
 
 
 # ----------------------------------------------------------------------------- phantoms
