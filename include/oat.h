@@ -43,6 +43,10 @@ extern "C" {
 #define OAT_F16  1
 #define OAT_BF16 2
 
+/* ---- shell-lattice point weights (oat_geometry.lattice_weights) ------------------- */
+#define OAT_LATTICE_UNIFORM    0
+#define OAT_LATTICE_EXACT_AREA 1
+
 typedef struct oat_plan_s *oat_plan;
 
 /*
@@ -62,6 +66,12 @@ typedef struct oat_plan_s *oat_plan;
  *   gruneisen           Gamma = beta c^2 / C_p (finite), scales D; D = Gamma/(8 pi c^2 dt^2)(...)
  *   data_dtype          OAT_F32, OAT_F16 or OAT_BF16: storage of u (project) and y (backproject)
  *   apply_d             1: H = D G (the model); 0: G only (the spherical Radon transform)
+ *   lattice_weights     weight of each shell-lattice point in G (Eq. dis_srt):
+ *                       OAT_LATTICE_UNIFORM (0): Delta_s^2 for every point (the Appendix);
+ *                       OAT_LATTICE_EXACT_AREA (1): the area of its ring's strip of the shell
+ *                       shared by the ring's N_j points, Delta_s 2 pi rho sin(theta_i) / N_j,
+ *                       which removes the bias of rounding 2 pi / dphi_i down to N_j.  The
+ *                       lattice itself is the same; G^T uses the same weights.
  */
 typedef struct {
     int nx, ny, nz;
@@ -77,6 +87,7 @@ typedef struct {
     double gruneisen;
     int data_dtype;
     int apply_d;
+    int lattice_weights;
 } oat_geometry;
 
 /* Sizes and counts of a plan (oat_plan_query). */

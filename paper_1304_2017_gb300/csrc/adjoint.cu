@@ -93,11 +93,11 @@ constexpr int kQueue = 64;   // per-warp queue of owned points (power of two, >=
 // Scatter one owned point (cell-local weights wx, wy, wz; first node b in the low 16 bits of
 // e.w, the point's shell s within the unit above them) with value wg[s].
 template <int S1, int S2>
-__device__ __forceinline__ void scatter8(int *shi, unsigned int *slo, float4 e, const float *wg) {
+__device__ __forceinline__ void scatter8(int *shi, unsigned int *slo, float4 e, const float *wg, float wr = 1.f) {
     const float wx = e.x, wy = e.y, wz = e.z;
     const int bs = __float_as_int(e.w);
     const int b = bs & 0xffff;
-    const float gq = wg[bs >> 16];
+    const float gq = wg[bs >> 16] * wr;
     const float ux = 1.f - wx, uy = 1.f - wy, uz = 1.f - wz;
     const float g00 = gq * uz * uy, g01 = gq * uz * wy, g10 = gq * wz * uy, g11 = gq * wz * wy;
     sadd(shi, slo, b, g00 * ux);           sadd(shi, slo, b + 1, g00 * wx);
@@ -106,7 +106,7 @@ __device__ __forceinline__ void scatter8(int *shi, unsigned int *slo, float4 e, 
     sadd(shi, slo, b + S2 + S1, g11 * ux); sadd(shi, slo, b + S2 + S1 + 1, g11 * wx);
 }
 
-template <int B, int DT>
+template <int B, int DT, bool AREA>
 __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
     extern __shared__ int shi[];   // node-sum high halves, low halves, segment slots, queues, views
     using NL = NodeLayout<B>;
@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
     SegSlot *slots = (SegSlot *)(shi + NN2);
     float4 *queues = (float4 *)(slots + kAdjThreads);
     BrickView *views = (BrickView *)(queues + kQueue * (kAdjThreads / 32));
+    float *wqueues = (float *)(views + kAdjThreads / 32);   // ring weights of queued points (AREA)
     const int nqc = (a.Q + a.qchunk - 1) / a.qchunk;
     const int brick = blockIdx.x / nqc;
     const int q0 = (blockIdx.x % nqc) * a.qchunk;
@@ -147,6 +148,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     SegSlot *ws = slots + warp * 32;
     float4 *wq = queues + warp * kQueue;
+    float *wrq = wqueues + warp * kQueue;
     __shared__ float s_wg[kAdjThreads / 32][kShells];
     float *wg = s_wg[warp];
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -198,15 +200,16 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
                 const int S = ring_windows(v, a.t.rings, gidx, a.O, rb2, blo, bhi, lane, wa0, wna, wb0, wnb, sincl);
                 for (int sc = 0, used = 0; sc < S; sc += used) {
                     int my_start, csh;
-                    const int total = segment_chunk<false>(a.t.xd + q, a.t.rings, a.t.anchors, gidx, shell, a.O, a.O_lo,
+                    const int total = segment_chunk<false>(a.t.xd + q, a.t.rings, a.t.anchors, AREA ? a.t.ring_w : nullptr,
+                                                           gidx, shell, a.O, a.O_lo,
                                                            L, sc, S, lane, wa0, wna, wb0, wnb, sincl, ws, my_start, used,
                                                            csh);
                     for (int f = 0; f < total; f += 32) {
                         int lc[3];
-                        float w[3];
+                        float w[3], wr;
                         bool own = false;
                         float4 ent;
-                        const int sh = segment_point(ws, f, lane, my_start, total, ex, ey, lc, w);
+                        const int sh = segment_point(ws, f, lane, my_start, total, ex, ey, lc, w, wr);
                         if (sh >= 0) {
                             own = (unsigned)lc[0] < (unsigned)E[0] && (unsigned)lc[1] < (unsigned)E[1] &&
                                   (unsigned)lc[2] < (unsigned)E[2];
@@ -214,11 +217,16 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
                         }
                         // queue the owned points; scatter them 32 at a time with every lane busy
                         const unsigned om = __ballot_sync(0xffffffffu, own);
-                        if (own) wq[(qt + __popc(om & lt_mask)) & (kQueue - 1)] = ent;
+                        if (own) {
+                            const int slot = (qt + __popc(om & lt_mask)) & (kQueue - 1);
+                            wq[slot] = ent;
+                            if (AREA) wrq[slot] = wr;
+                        }
                         qt += __popc(om);
                         __syncwarp();
                         if (qt - qh >= 32) {
-                            scatter8<S1, S2>(shi, slo, wq[(qh + lane) & (kQueue - 1)], wg);
+                            const int slot = (qh + lane) & (kQueue - 1);
+                            scatter8<S1, S2>(shi, slo, wq[slot], wg, AREA ? wrq[slot] : 1.f);
                             qh += 32;
                             __syncwarp();
                         }
@@ -226,7 +234,10 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
                     __syncwarp();
                 }
             }
-            if (lane < qt - qh) scatter8<S1, S2>(shi, slo, wq[(qh + lane) & (kQueue - 1)], wg);
+            if (lane < qt - qh) {
+                const int slot = (qh + lane) & (kQueue - 1);
+                scatter8<S1, S2>(shi, slo, wq[slot], wg, AREA ? wrq[slot] : 1.f);
+            }
             __syncwarp();
         }
         __syncthreads();
@@ -283,11 +294,21 @@ static int backproject_with(Plan &p, const void *data, float *vol, cudaStream_t 
     const bool prof = p.profiling && p.ev_used[1] + 2 <= (int)p.ev[1].size();
     if (prof) cudaEventRecord(p.ev[1][p.ev_used[1]], s);
     const unsigned grid = (unsigned)p.adj.items;
-    switch (dtype) {
-        case OAT_F32: k_brick_gather_t<kBA, OAT_F32><<<grid, kAdjThreads, p.adj.smem, s>>>(a); break;
-        case OAT_F16: k_brick_gather_t<kBA, OAT_F16><<<grid, kAdjThreads, p.adj.smem, s>>>(a); break;
-        default: k_brick_gather_t<kBA, OAT_BF16><<<grid, kAdjThreads, p.adj.smem, s>>>(a); break;
+#define OAT_GT(DTV, AR) k_brick_gather_t<kBA, DTV, AR><<<grid, kAdjThreads, p.adj.smem, s>>>(a)
+    if (p.area) {
+        switch (dtype) {
+            case OAT_F32: OAT_GT(OAT_F32, true); break;
+            case OAT_F16: OAT_GT(OAT_F16, true); break;
+            default: OAT_GT(OAT_BF16, true); break;
+        }
+    } else {
+        switch (dtype) {
+            case OAT_F32: OAT_GT(OAT_F32, false); break;
+            case OAT_F16: OAT_GT(OAT_F16, false); break;
+            default: OAT_GT(OAT_BF16, false); break;
+        }
     }
+#undef OAT_GT
     if (prof) { cudaEventRecord(p.ev[1][p.ev_used[1] + 1], s); p.ev_used[1] += 2; }
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_backproject: k_brick_gather_t: ") + cudaGetErrorString(e));
@@ -344,16 +365,20 @@ int launch_backproject_static(Plan &p, const void *data, float *vol, cudaStream_
     return backproject_with(p, data, vol, s, (long long *)(w + kStaticHeader), (unsigned int *)w);
 }
 
-size_t adjoint_smem_bytes() {
+size_t adjoint_smem_bytes(bool area) {
     return sizeof(int) * NodeLayout<kBA>::NN2 + sizeof(SegSlot) * kAdjThreads +
-           sizeof(float4) * kQueue * (kAdjThreads / 32) + sizeof(BrickView) * (kAdjThreads / 32);
+           sizeof(float4) * kQueue * (kAdjThreads / 32) + sizeof(BrickView) * (kAdjThreads / 32) +
+           (area ? sizeof(float) * kQueue * (kAdjThreads / 32) : 0);
 }
 
 int set_adjoint_attributes() {
-    const int bytes = (int)adjoint_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(k_brick_gather_t<kBA, OAT_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_brick_gather_t<kBA, OAT_F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_brick_gather_t<kBA, OAT_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    const int b0 = (int)adjoint_smem_bytes(false), b1 = (int)adjoint_smem_bytes(true);
+    cudaError_t e = cudaSuccess;
+#define OAT_ATTR(DTV, AR, BYTES) \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_brick_gather_t<kBA, DTV, AR>, cudaFuncAttributeMaxDynamicSharedMemorySize, BYTES)
+    OAT_ATTR(OAT_F32, false, b0); OAT_ATTR(OAT_F16, false, b0); OAT_ATTR(OAT_BF16, false, b0);
+    OAT_ATTR(OAT_F32, true, b1); OAT_ATTR(OAT_F16, true, b1); OAT_ATTR(OAT_BF16, true, b1);
+#undef OAT_ATTR
     return e == cudaSuccess ? OAT_OK : set_error(OAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
 }
 

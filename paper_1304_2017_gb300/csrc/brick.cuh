@@ -192,8 +192,9 @@ struct __align__(16) SegSlot {
     int I[3];            // anchor cell I, relative to the brick's lowest cell L
     float xa, ya;        // anchor local coordinates (hi parts)
     float dphi, dphi_lo;
-    int mp;              // m = j - j_A of the segment's first point | poly << 8 | shell << 9
-    int start;           // position of the segment's first point in the chunk's candidate list
+    int mp;              // m = j - j_A of the segment's first point | poly << 5 | shell << 6 |
+                         // position of that point in the chunk's candidate list << 8
+    float w;             // the ring's point weight over Delta_s^2 (1 with uniform weights)
 };
 
 __device__ __forceinline__ int anchor_segments(int lo, int n) {
@@ -230,7 +231,8 @@ __device__ __forceinline__ int ring_windows(const BrickView &v, const Ring *__re
 // has shell cshell.  Warp-collective.
 template <bool ONE_SHELL>
 __device__ __forceinline__ int segment_chunk(const Xdcr *__restrict__ xq, const Ring *__restrict__ rings,
-                                             const float4 *__restrict__ anchors, int gidx, int shell,
+                                             const float4 *__restrict__ anchors, const float *__restrict__ ring_w,
+                                             int gidx, int shell,
                                              const float Oh[3], const float Ol[3], const int L[3], int sc, int S,
                                              int lane, int wa0, int wna, int wb0, int wnb, int sincl, SegSlot *ws,
                                              int &my_start, int &used, int &cshell) {
@@ -277,8 +279,8 @@ __device__ __forceinline__ int segment_chunk(const Xdcr *__restrict__ xq, const 
         for (int d = 0; d < 3; ++d) { sl.f[d] = fr[d]; sl.I[d] = I[d] - L[d]; }
         sl.xa = xy.x; sl.ya = xy.z;
         sl.dphi = rg.dphi; sl.dphi_lo = rg.dphi_lo;
-        sl.mp = (j0 - (t << kAnchorShift)) | (rg.poly << 8) | (rshell << 9);
-        sl.start = incl - cnt;
+        sl.mp = (j0 - (t << kAnchorShift)) | (rg.poly << 5) | (rshell << 6) | ((incl - cnt) << 8);
+        sl.w = ring_w ? __ldg(ring_w + rg_idx) : 1.f;
     }
     my_start = cnt > 0 ? incl - cnt : 0x7fffffff;
     __syncwarp();
@@ -286,11 +288,12 @@ __device__ __forceinline__ int segment_chunk(const Xdcr *__restrict__ xq, const 
 }
 
 // Candidate f + lane of a chunk: its cell relative to the brick's lowest cell (lc), its position
-// in that cell (w) and its shell within the unit (returned; -1 for lanes past the end of the
-// list), through the shared lattice-point functions (ex, ey: the transducer's frame, hi parts).
-// Warp-collective.
+// in that cell (w), its ring's weight factor (wr) and its shell within the unit (returned; -1
+// for lanes past the end of the list), through the shared lattice-point functions (ex, ey: the
+// transducer's frame, hi parts).  Warp-collective.
 __device__ __forceinline__ int segment_point(const SegSlot *ws, int f, int lane, int my_start, int total,
-                                             const float ex[3], const float ey[3], int lc[3], float w[3]) {
+                                             const float ex[3], const float ey[3], int lc[3], float w[3],
+                                             float &wr) {
     const int before = __popc(__ballot_sync(0xffffffffu, my_start <= f));
     const unsigned inside =
         __reduce_or_sync(0xffffffffu, (my_start > f && my_start < f + 32) ? (1u << (my_start - f)) : 0u);
@@ -298,12 +301,13 @@ __device__ __forceinline__ int segment_point(const SegSlot *ws, int f, int lane,
     if (cidx >= total) return -1;
     const SegSlot &sl = ws[before - 1 + __popc(inside & ((2u << lane) - 1u))];
     const int mp = sl.mp;
-    const float3 R = anchor_offset(sl.f, sl.xa, sl.ya, ex, ey, sl.dphi, sl.dphi_lo, (mp >> 8) & 1,
-                                   (mp & 0xff) + (cidx - sl.start));
+    const float3 R = anchor_offset(sl.f, sl.xa, sl.ya, ex, ey, sl.dphi, sl.dphi_lo, (mp >> 5) & 1,
+                                   (mp & kAnchorMask) + (cidx - (mp >> 8)));
     const float fx = floorf(R.x), fy = floorf(R.y), fz = floorf(R.z);
     lc[0] = sl.I[0] + (int)fx; lc[1] = sl.I[1] + (int)fy; lc[2] = sl.I[2] + (int)fz;
     w[0] = __fsub_rn(R.x, fx); w[1] = __fsub_rn(R.y, fy); w[2] = __fsub_rn(R.z, fz);
-    return mp >> 9;
+    wr = sl.w;
+    return (mp >> 6) & 3;
 }
 
 // Lowest cell L and cell counts E (<= bs) of brick id in a grid of nb[3] bricks (x fastest)

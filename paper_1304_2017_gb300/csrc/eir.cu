@@ -96,7 +96,7 @@ int set_eir_attributes(const Plan &p) {
 
 int launch_apply_d_eir(Plan &p, void *data, cudaStream_t s) {
     const size_t smem = eir_smem_bytes(p);
-    const double bp = (double)p.max_shell_points, ds2 = p.g.spacing_mm * p.g.spacing_mm;
+    const double bp = p.fwd_bound, ds2 = p.g.spacing_mm * p.g.spacing_mm;
     const long long *g = (const long long *)p.d_gacc;
     const int dt = p.g.data_dtype;
 #define OAT_EIR(DTV, AD) k_apply_d_eir<DTV, AD><<<(unsigned)p.Q, kEirThreads, smem, s>>>( \

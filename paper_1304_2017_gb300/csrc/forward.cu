@@ -62,7 +62,7 @@ struct FwdArgs {
     int qchunk, kspan;
     float O[3], O_lo[3];
     float R0, dR;
-    double bound_pts;             // max lattice points of one shell
+    double bound_pts;             // max sum of the point weights (over Delta_s^2) of one shell
     unsigned long long *count;    // COUNT mode: owned lattice points
 };
 
@@ -84,7 +84,7 @@ __device__ __forceinline__ void flush_shell(float s, float e, double scale, int 
 
 // COUNT: instead of interpolating, count the points each brick owns (the bricks tile the cells
 // [-1, n-1]^3, so the total is the number of lattice points whose stencil touches the grid).
-template <int B, bool COUNT>
+template <int B, bool COUNT, bool AREA>
 __global__ void __launch_bounds__(kFwdThreads, 1) k_brick_gather(FwdArgs a) {
     extern __shared__ float sv[];   // (B+1)^3 nodes of the brick, then the warps' segment slots
     constexpr int S1 = B + 1, S2 = (B + 1) * (B + 1), NN = (B + 1) * (B + 1) * (B + 1);
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_brick_gather(FwdArgs a) {
             const int S = ring_windows(v, a.t.rings, gidx, a.O, rb2, blo, bhi, lane, wa0, wna, wb0, wnb, sincl);
             for (int sc = 0, used = 0; sc < S; sc += used) {
                 int my_start, csh;
-                const int total = segment_chunk<true>(a.t.xd + q, a.t.rings, a.t.anchors, gidx, shell, a.O, a.O_lo, L,
+                const int total = segment_chunk<true>(a.t.xd + q, a.t.rings, a.t.anchors, AREA ? a.t.ring_w : nullptr, gidx, shell, a.O, a.O_lo, L,
                                                       sc, S, lane, wa0, wna, wb0, wnb, sincl, ws, my_start, used, csh);
                 if (csh != cur) {
                     if (!COUNT && cur >= 0) flush_shell(acc, err, scale, lane, a.gacc + (size_t)q * a.K + kb + cur);
@@ -175,14 +175,15 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_brick_gather(FwdArgs a) {
                 }
                 for (int f = 0; f < total; f += 32) {
                     int lc[3];
-                    float w[3];
-                    if (segment_point(ws, f, lane, my_start, total, ex, ey, lc, w) < 0) continue;
+                    float w[3], wr;
+                    if (segment_point(ws, f, lane, my_start, total, ex, ey, lc, w, wr) < 0) continue;
                     if ((unsigned)lc[0] < (unsigned)E[0] && (unsigned)lc[1] < (unsigned)E[1] && (unsigned)lc[2] < (unsigned)E[2]) {
                         if (COUNT) { ++owned; continue; }
                         const float *sp = sv + lc[2] * S2 + lc[1] * S1 + lc[0];
                         const float c00 = lerp1(sp[0], sp[1], w[0]), c01 = lerp1(sp[S1], sp[S1 + 1], w[0]);
                         const float c10 = lerp1(sp[S2], sp[S2 + 1], w[0]), c11 = lerp1(sp[S2 + S1], sp[S2 + S1 + 1], w[0]);
-                        kadd(acc, err, lerp1(lerp1(c00, c01, w[1]), lerp1(c10, c11, w[1]), w[2]));
+                        const float v = lerp1(lerp1(c00, c01, w[1]), lerp1(c10, c11, w[1]), w[2]);
+                        kadd(acc, err, AREA ? wr * v : v);
                     }
                 }
                 __syncwarp();
@@ -220,10 +221,13 @@ size_t forward_smem_bytes() {
 }
 
 int set_forward_attributes() {
-    cudaError_t e = cudaFuncSetAttribute(k_brick_gather<kBF, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_brick_gather<kBF, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)forward_smem_bytes());
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_brick_gather<kBF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_brick_gather<kBF, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)forward_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_brick_gather<kBF, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)forward_smem_bytes());
     return e == cudaSuccess ? OAT_OK : set_error(OAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
 }
@@ -236,7 +240,7 @@ static void fill_forward_args(const Plan &p, const float *vol, FwdArgs &a) {
     for (int d = 0; d < 3; ++d) { a.nb[d] = p.fwd.nb[d]; a.bs[d] = p.fwd.bs[d]; a.O[d] = p.O[d]; a.O_lo[d] = p.O_lo[d]; }
     a.qchunk = p.fwd.qchunk; a.kspan = p.fwd.kspan;
     a.R0 = p.R0; a.dR = p.dR;
-    a.bound_pts = (double)p.max_shell_points;
+    a.bound_pts = p.fwd_bound;
     a.count = nullptr;
 }
 
@@ -250,7 +254,8 @@ int launch_project(Plan &p, const float *vol, void *data, cudaStream_t s) {
     fill_forward_args(p, vol, a);
     const bool prof = p.profiling && p.ev_used[0] + 2 <= (int)p.ev[0].size();
     if (prof) cudaEventRecord(p.ev[0][p.ev_used[0]], s);
-    k_brick_gather<kBF, false><<<(unsigned)p.fwd.items, kFwdThreads, p.fwd.smem, s>>>(a);
+    if (p.area) k_brick_gather<kBF, false, true><<<(unsigned)p.fwd.items, kFwdThreads, p.fwd.smem, s>>>(a);
+    else k_brick_gather<kBF, false, false><<<(unsigned)p.fwd.items, kFwdThreads, p.fwd.smem, s>>>(a);
     if (prof) { cudaEventRecord(p.ev[0][p.ev_used[0] + 1], s); p.ev_used[0] += 2; }
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_project: k_brick_gather: ") + cudaGetErrorString(e));
@@ -258,7 +263,7 @@ int launch_project(Plan &p, const float *vol, void *data, cudaStream_t s) {
     const size_t n = (size_t)p.Q * p.K;
     const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
     const int dt = p.g.data_dtype;
-    const double bp = (double)p.max_shell_points, ds2 = p.g.spacing_mm * p.g.spacing_mm;
+    const double bp = p.fwd_bound, ds2 = p.g.spacing_mm * p.g.spacing_mm;
     const long long *g = (const long long *)p.d_gacc;
 #define OAT_APPLY(DTV, AD) k_apply_d_fix<DTV, AD><<<blocks, 256, 0, s>>>(g, p.t.wD64, data, p.Q, p.K, p.d_amax, bp, ds2)
     if (p.g.apply_d) {
@@ -281,7 +286,7 @@ int count_grid_points(Plan &p, long long *out) {
     a.count = p.d_count;
     cudaError_t e = cudaMemset(p.d_count, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) {
-        k_brick_gather<kBF, true><<<(unsigned)p.fwd.items, kFwdThreads, p.fwd.smem>>>(a);
+        k_brick_gather<kBF, true, false><<<(unsigned)p.fwd.items, kFwdThreads, p.fwd.smem>>>(a);
         e = cudaGetLastError();
     }
     unsigned long long h = 0;

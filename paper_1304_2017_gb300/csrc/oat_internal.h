@@ -58,6 +58,7 @@ struct DevTables {
     const float *Rk;          // [K] rho_k / Delta_s (may be <= 0)
     const float *wD;          // [K] C_D / tau_k, 0 where tau_k <= 0
     const double *wD64;       // [K] the same in double (forward D)
+    const float *ring_w;      // [rings] point weight / Delta_s^2 (exact strip areas); null: 1
 };
 
 // Brick tiling of the cell range [-1, n-1]^3 for one direction: nb bricks per axis of bs cells
@@ -87,6 +88,8 @@ struct Plan {
     float R0 = 0, dR = 0;        // rho_0 / Delta_s and c dt / Delta_s
     long long n_rings = 0, n_anchors = 0, points_ball = 0;
     long long max_shell_points = 0;   // largest N_i-ring lattice of one shell (fixed-point bound)
+    bool area = false;                // exact strip-area point weights (ring_w)
+    double fwd_bound = 0.0;           // max over shells of the sum of point weights / Delta_s^2
     float gscale = 1.f;               // max |g'| / max |y|: 2 max_k C_D/tau_k with D, 1 without
     int adj_qpass = 1;                // transducers per backprojector pass (bounds the 32-bit halves)
     BrickCfg fwd, adj;                 // brick tilings of the projector and the backprojector
@@ -139,7 +142,7 @@ int launch_fbp(Plan &p, const void *data, float *vol, cudaStream_t s);
 int set_adjoint_attributes();
 int set_forward_attributes();
 size_t forward_smem_bytes();
-size_t adjoint_smem_bytes();
+size_t adjoint_smem_bytes(bool area);
 
 constexpr int kMaxEvents = 4096;
 

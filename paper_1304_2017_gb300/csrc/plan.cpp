@@ -86,6 +86,8 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
         return set_error(OAT_ERR_INVALID_ARG, "oat_plan_create: data_dtype must be OAT_F32, OAT_F16 or OAT_BF16");
     if (g.apply_d != 0 && g.apply_d != 1)
         return set_error(OAT_ERR_INVALID_ARG, "oat_plan_create: apply_d must be 0 or 1");
+    if (g.lattice_weights != OAT_LATTICE_UNIFORM && g.lattice_weights != OAT_LATTICE_EXACT_AREA)
+        return set_error(OAT_ERR_INVALID_ARG, "oat_plan_create: lattice_weights must be OAT_LATTICE_UNIFORM or OAT_LATTICE_EXACT_AREA");
 
     Plan *p = new (std::nothrow) Plan();
     if (!p) return set_error(OAT_ERR_OOM, "oat_plan_create: host allocation failed");
@@ -137,7 +139,10 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
     // ring: points j = 32 t, local coordinates a (cos(j dphi), sin(j dphi)) as float pairs
     const int C = p->n_cls;
     std::vector<Ring> rings;
+    std::vector<float> ring_w;          // exact strip areas: point weight / Delta_s^2 per ring
     std::vector<float4> anchors;
+    const bool area = g.lattice_weights == OAT_LATTICE_EXACT_AREA;
+    double wsum_max = 0.0, wring_max = 0.0;
     std::vector<int> ring_off((size_t)C * K), ring_cnt((size_t)C * K);
     p->cls_points.assign((size_t)C * K, 0);
     for (int c = 0; c < C; ++c) {
@@ -159,6 +164,7 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
                 return set_error(OAT_ERR_UNSUPPORTED, "oat_plan_create: lattice tables exceed 2^31 rings");
             }
             long long npts = 0;
+            double wsum = 0.0;
             for (int i = 0; i < ni; ++i) {
                 double th = i * dth;
                 double st = std::sin(th);
@@ -187,7 +193,16 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
                 }
                 rings.push_back(rr);
                 npts += nj;
+                if (area) {
+                    // the strip of ring i (polar width dtheta, i.e. Delta_s on the shell; length
+                    // 2 pi rho sin theta_i) shared by its N_j points, over Delta_s^2
+                    const double wi = nj > 0 ? 2.0 * M_PI * a / nj : 0.0;
+                    ring_w.push_back((float)wi);
+                    wsum += (double)(float)wi * nj;
+                    wring_max = std::max(wring_max, (double)(float)wi);
+                }
             }
+            wsum_max = std::max(wsum_max, wsum);
             ring_cnt[ck] = ni;
             p->cls_points[ck] = npts;
         }
@@ -207,6 +222,9 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
 
     p->max_shell_points = 0;
     for (long long np : p->cls_points) p->max_shell_points = std::max(p->max_shell_points, np);
+    // bound of |G alpha| / max|alpha| in units of Delta_s^2 (the projector's fixed-point range)
+    p->area = area;
+    p->fwd_bound = area ? wsum_max * (1.0 + 1e-6) : (double)p->max_shell_points;
 
     // brick tilings of the cells [-1, n-1] for the two directions
     auto tile = [&](BrickCfg &bc, int B, size_t node_bytes) {
@@ -231,7 +249,7 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
     tile(p->fwd, kBF, sizeof(float));
     p->fwd.smem = forward_smem_bytes();
     tile(p->adj, kBA, 2 * sizeof(int));
-    p->adj.smem = adjoint_smem_bytes();
+    p->adj.smem = adjoint_smem_bytes(area);
     {
         // contributions one transducer adds to one node: 8 cells x (shells crossing a cell:
         // diameter sqrt(3) over the shell spacing, + 2) x (2 rings x 3 points, + margin)
@@ -258,12 +276,14 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
     double wmax = 0.0;
     for (int k = 0; k < K; ++k) wmax = std::max(wmax, (double)wD[k]);
     p->gscale = g.apply_d ? (float)(2.0 * wmax * (1.0 + 1e-6)) : 1.f;
+    if (area) p->gscale = (float)((double)p->gscale * wring_max * (1.0 + 1e-6));
 
     // one device blob for every table
     std::vector<unsigned char> blob;
     size_t o_rings = push_bytes(blob, rings), o_off = push_bytes(blob, ring_off), o_cnt = push_bytes(blob, ring_cnt);
     size_t o_xd = push_bytes(blob, xd), o_an = push_bytes(blob, anchors);
     size_t o_rk = push_bytes(blob, Rk), o_wd = push_bytes(blob, wD), o_wd64 = push_bytes(blob, wD64);
+    size_t o_rw = push_bytes(blob, ring_w);
     std::vector<float4>().swap(anchors);
     p->table_bytes = (long long)blob.size();
 
@@ -324,6 +344,7 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
     p->t.Rk = (const float *)(base + o_rk);
     p->t.wD = (const float *)(base + o_wd);
     p->t.wD64 = (const double *)(base + o_wd64);
+    p->t.ring_w = area ? (const float *)(base + o_rw) : nullptr;
     *out = p;
     return OAT_OK;
 }

@@ -37,7 +37,8 @@ class oat_geometry(ctypes.Structure):
                 ("n_transducers", ctypes.c_int), ("positions_mm", ctypes.POINTER(ctypes.c_double)),
                 ("n_samples", ctypes.c_int), ("fs_mhz", ctypes.c_double), ("t_min_us", ctypes.c_double),
                 ("c_mm_per_us", ctypes.c_double), ("support_radius_mm", ctypes.c_double),
-                ("gruneisen", ctypes.c_double), ("data_dtype", ctypes.c_int), ("apply_d", ctypes.c_int)]
+                ("gruneisen", ctypes.c_double), ("data_dtype", ctypes.c_int), ("apply_d", ctypes.c_int),
+                ("lattice_weights", ctypes.c_int)]
 
 
 class oat_stats(ctypes.Structure):
@@ -97,7 +98,7 @@ def make_geometry_struct(geom, data_dtype=OAT_F32, apply_d=True):
     s = oat_geometry(geom.nx, geom.ny, geom.nz, geom.spacing_mm, (ctypes.c_double * 3)(*geom.origin_mm),
                      pos.shape[0], pos.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), geom.n_samples,
                      geom.fs_mhz, geom.t_min_us, geom.c_mm_per_us, geom.support_radius_mm, geom.gruneisen,
-                     int(data_dtype), int(bool(apply_d)))
+                     int(data_dtype), int(bool(apply_d)), int(getattr(geom, "lattice_weights", 0)))
     return s, pos
 
 

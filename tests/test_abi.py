@@ -54,7 +54,7 @@ def _struct(oat, geom, **kw):
     ("nx", 0, -1), ("n_samples", 2, -1), ("spacing_mm", 0.0, -1), ("spacing_mm", float("nan"), -1),
     ("fs_mhz", -1.0, -1), ("c_mm_per_us", 0.0, -1), ("t_min_us", -0.5, -1), ("data_dtype", 7, -1),
     ("apply_d", 2, -1), ("support_radius_mm", 30.0, -2), ("t_min_us", 1000.0, -2),
-    ("gruneisen", float("inf"), -1),
+    ("gruneisen", float("inf"), -1), ("lattice_weights", 2, -1), ("lattice_weights", -1, -1),
 ])
 def test_invalid_geometry_rejected_on_host(oat, field, value, code):
     geom = W.make_geometry(8, 0.5, 2, 2, 10.0, 32)
