@@ -304,6 +304,74 @@ def run_fbp(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sph(args):
+    """Spherical-voxel model H_sph + H_sph^T (Eqs. dis_sph, sphbwd) on the paper's simulation grid
+    (210 x 210 x 440 at 0.14 mm), its 64 x 90 scan on 65 mm and 511 frequencies in (0, 5] MHz:
+    complex voxel-transducer-frequency terms per second, CUDA events around W untimed and K timed
+    steps (one H_sph and one H_sph^T each); the FP64 reference timed on one transducer x 8
+    frequencies.  --sph-transducers n keeps n transducers spread over the scan (small captures)."""
+    import torch
+    from paper_1304_2017_gb300 import oat
+    from paper_1304_2017_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    geom = W.sph_config()
+    if args.sph_transducers:
+        geom = geom.subset(np.linspace(0, geom.n_transducers - 1, args.sph_transducers).round().astype(int))
+    L, f0, df = 511, 5.0 / 511, 5.0 / 511
+    alpha = torch.from_numpy(W.phantom_sph(geom)).to(dev)
+    op = oat.SphOp(geom, L, f0, df)
+    u = torch.empty(op.data_shape, dtype=torch.complex64, device=dev)
+    a = torch.empty(op.vol_shape, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        op.project(alpha, out=u)
+        op.backproject(u, out=a)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * args.steps)]
+    clk = ClockSampler(0)
+    torch.cuda.synchronize(dev)
+    clk.start()
+    for i in range(args.steps):
+        ev[3 * i].record()
+        op.project(alpha, out=u)
+        ev[3 * i + 1].record()
+        op.backproject(u, out=a)
+        ev[3 * i + 2].record()
+    torch.cuda.synchronize(dev)
+    clocks = clk.stop()
+    t_fwd = sum(ev[3 * i].elapsed_time(ev[3 * i + 1]) for i in range(args.steps)) * 1e-3 / args.steps
+    t_bwd = sum(ev[3 * i + 1].elapsed_time(ev[3 * i + 2]) for i in range(args.steps)) * 1e-3 / args.steps
+    terms = float(geom.n_voxels) * geom.n_transducers * L
+    peaks, src = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = {"tflops": N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12,
+            "source": f"{src}: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz"}
+    dom, dom_t = ("k_sph_bwd (H_sph^T)", t_bwd) if t_bwd >= t_fwd else ("k_sph_fwd (H_sph)", t_fwd)
+    line = {"metric": "H_sph+H_sph^T complex terms/s (spherical-voxel model, Eqs. dis_sph and sphbwd)",
+            "value": 2 * terms / (t_fwd + t_bwd), "unit": "terms/s", "ms_per_step": (t_fwd + t_bwd) * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": W.SPH_DESCRIPTION if not args.sph_transducers else
+                       W.SPH_DESCRIPTION + f", {geom.n_transducers} transducers", "terms_per_operator": terms},
+            "seconds": {"H_sph": t_fwd, "H_sph^T": t_bwd},
+            "roofline": {"bound": "alu", "achieved": 8.0 * terms / dom_t * 1e-12, "peak": peak["tflops"],
+                         "unit": "TFLOP/s", "frac": 8.0 * terms / dom_t * 1e-12 / peak["tflops"], "traffic": None,
+                         "kernel": dom, "flop_per_term": 8.0, "peak_source": peak["source"]},
+            "clocks": clocks}
+    if not args.no_cpu_baseline:
+        from oracle import sph as S
+        freqs = f0 + df * np.arange(L)
+        an = alpha.cpu().numpy()
+        t0 = time.perf_counter()
+        S.H_sph(geom, an, freqs[::64], qs=[0])
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": float(geom.n_voxels) * len(freqs[::64]) / dt, "unit": "terms/s",
+                                "cores": 1, "kind": "oracle",
+                                "sample": f"1 transducer x {len(freqs[::64])} frequencies, full grid, numpy FP64, "
+                                          f"{dt:.1f} s"}
+    op.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_learned(args):
     """PLS-TV time to a 1e-3 relative data residual from zero and from the learned warm start."""
     from paper_1304_2017_gb300 import warmstart
@@ -354,6 +422,9 @@ def main():
     ap.add_argument("--pls", action="store_true",
                     help="PLS-TV (FISTA-TV) time to a 1e-3 relative data residual on the 160^3 workload")
     ap.add_argument("--pls-iters", type=int, default=400, help="iteration cap of --pls")
+    ap.add_argument("--sph", action="store_true",
+                    help="spherical-voxel model H_sph + H_sph^T on the paper's 210 x 210 x 440 grid")
+    ap.add_argument("--sph-transducers", type=int, default=0, help="--sph on this many transducers (0: all)")
     ap.add_argument("--capture", action="store_true",
                     help="small case for ncu captures: the 256^3 workload on 64 transducers, H and H^T twice")
     args = ap.parse_args()
@@ -367,6 +438,8 @@ def main():
         return run_pls(args)
     if args.fbp:
         return run_fbp(args)
+    if args.sph:
+        return run_sph(args)
 
     import torch
     import torch.distributed as dist

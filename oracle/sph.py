@@ -85,9 +85,11 @@ def H_sph_t(geom, u, freqs_mhz, eir=None, nodes=None):
         nd = np.asarray(nodes, np.int64).reshape(-1, 3)
         rn = np.stack([xs[nd[:, 0]], ys[nd[:, 1]], zs[nd[:, 2]]], axis=1)
     out = np.zeros(len(rn))
+    w = u * np.conj(p0)[None, :]                                  # u~_{q,l} conj(p~0(f_l))
     for q in range(geom.n_transducers):
         d = np.linalg.norm(rn - geom.positions_mm[q], axis=1)
-        for l in range(len(f)):
-            hc = np.exp(2j * math.pi * f[l] * d / geom.c_mm_per_us) / (2.0 * math.pi * d)
-            out += (u[q, l] * np.conj(p0[l]) * hc).real
+        for c0 in range(0, len(rn), 4096):                        # nodes in chunks, all frequencies at once
+            dc = d[c0:c0 + 4096]
+            hc = np.exp(2j * math.pi * f[:, None] * dc[None, :] / geom.c_mm_per_us) / (2.0 * math.pi * dc[None, :])
+            out[c0:c0 + 4096] += (w[q] @ hc).real
     return out.reshape(geom.vol_shape) if nodes is None else out

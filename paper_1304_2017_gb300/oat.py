@@ -71,8 +71,13 @@ def _load():
     lib.oat_dot.argtypes = [ll, vp, vp, vp, vp]
     lib.oat_tv_value.argtypes = [i32, i32, i32, vp, vp, vp]
     lib.oat_probe_read.argtypes = [vp, ll, i32, vp, vp]
+    lib.oat_sph_create.argtypes = [ctypes.POINTER(oat_geometry), i32, ctypes.c_double, ctypes.c_double,
+                                   ctypes.POINTER(ctypes.c_double), i32, ctypes.POINTER(vp)]
+    lib.oat_sph_project.argtypes = [vp, vp, vp, vp]
+    lib.oat_sph_backproject.argtypes = [vp, vp, vp, vp]
+    lib.oat_sph_destroy.argtypes = [vp]
     for name in ("oat_fista_residual", "oat_tv_prox", "oat_fista_momentum", "oat_dot", "oat_tv_value",
-                 "oat_probe_read"):
+                 "oat_probe_read", "oat_sph_create", "oat_sph_project", "oat_sph_backproject", "oat_sph_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     lib.oat_last_error.restype = ctypes.c_char_p
     lib.oat_version.restype = ctypes.c_int
@@ -197,6 +202,31 @@ def oat_probe_read(buf, n_bytes, reps, sink, stream=0):
     return _check(lib.oat_probe_read(_p(buf), n_bytes, reps, _p(sink), _p(stream)))
 
 
+# ---- spherical-voxel model (include/oat_sph.h) ---------------------------------------------
+
+def oat_sph_create(geom_struct, n_freq, f0_mhz, df_mhz, eir=None, device=0):
+    h = ctypes.c_void_p()
+    e = None
+    if eir is not None:
+        e = np.ascontiguousarray(np.stack([np.real(eir), np.imag(eir)], axis=1), dtype=np.float64)
+    ptr = e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if e is not None else None
+    _check(lib.oat_sph_create(ctypes.byref(geom_struct), int(n_freq), float(f0_mhz), float(df_mhz), ptr, int(device),
+                              ctypes.byref(h)))
+    return h
+
+
+def oat_sph_project(handle, d_alpha, d_u, stream=0):
+    return _check(lib.oat_sph_project(handle, _p(d_alpha), _p(d_u), _p(stream)))
+
+
+def oat_sph_backproject(handle, d_u, d_alpha, stream=0):
+    return _check(lib.oat_sph_backproject(handle, _p(d_u), _p(d_alpha), _p(stream)))
+
+
+def oat_sph_destroy(handle):
+    return _check(lib.oat_sph_destroy(handle))
+
+
 # ---- torch wrapper ---------------------------------------------------------------------
 
 _DT = {OAT_F32: "float32", OAT_F16: "float16", OAT_BF16: "bfloat16"}
@@ -299,3 +329,61 @@ class Plan:
 
     def kernel_time(self, which, reset=False):
         return oat_plan_kernel_time(self.handle, which, reset)
+
+
+class SphOp:
+    """The spherical-voxel model for one geometry and L frequencies f_l = f0 + l df:
+    ``project(alpha) -> u`` (complex64 [Q][L]) and ``backproject(u) -> alpha'`` (float32)."""
+
+    def __init__(self, geom, n_freq, f0_mhz, df_mhz, eir=None, device=None):
+        import torch
+        self._torch = torch
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(device)
+        self.geom = geom
+        self.n_freq = int(n_freq)
+        self.freqs = float(f0_mhz) + float(df_mhz) * np.arange(self.n_freq)
+        self._s, self._pos = make_geometry_struct(geom)
+        self.handle = oat_sph_create(self._s, n_freq, f0_mhz, df_mhz, eir, self.device)
+        self.vol_shape = (geom.nz, geom.ny, geom.nx)
+        self.data_shape = (geom.n_transducers, self.n_freq)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            oat_sph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self):
+        return self._torch.cuda.current_stream(self.device).cuda_stream
+
+    def _checked(self, t, shape, dtype, name):
+        torch = self._torch
+        if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.device.index != self.device:
+            raise ValueError(f"{name}: expected a CUDA tensor on device {self.device}")
+        if tuple(t.shape) != tuple(shape) or t.dtype != dtype or not t.is_contiguous():
+            raise ValueError(f"{name}: expected contiguous {dtype} of shape {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
+
+    def project(self, alpha, out=None):
+        torch = self._torch
+        self._checked(alpha, self.vol_shape, torch.float32, "alpha")
+        if out is None:
+            out = torch.empty(self.data_shape, dtype=torch.complex64, device=alpha.device)
+        self._checked(out, self.data_shape, torch.complex64, "out")
+        oat_sph_project(self.handle, alpha.data_ptr(), out.data_ptr(), self._stream())
+        return out
+
+    def backproject(self, u, out=None):
+        torch = self._torch
+        self._checked(u, self.data_shape, torch.complex64, "u")
+        if out is None:
+            out = torch.empty(self.vol_shape, dtype=torch.float32, device=u.device)
+        self._checked(out, self.vol_shape, torch.float32, "out")
+        oat_sph_backproject(self.handle, u.data_ptr(), out.data_ptr(), self._stream())
+        return out

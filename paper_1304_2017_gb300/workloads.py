@@ -299,6 +299,23 @@ def config(name: str) -> Geometry:
     return CONFIGS[name]()
 
 
+SPH_DESCRIPTION = ("210 x 210 x 440 @ 0.14 mm, 9 spheres, 64 rings x 90 views on 65 mm, "
+                   "511 frequencies in (0, 5] MHz, c=1.54")
+
+
+def sph_config() -> Geometry:
+    """The spherical-voxel workload: the grid of the paper's simulation studies (210 x 210 x 440
+    nodes at 0.14 mm, Sec. IV), the 64 rings x 90 views subset of its spherical scan on 65 mm, and
+    its speed of sound 1.54 mm/us.  The time-sampling fields are unused by that model."""
+    return make_geometry((210, 210, 440), 0.14, 64, 90, 65.0, 16, c=1.54)
+
+
+def phantom_sph(geom: Geometry, seed=1304):
+    """Nine uniform spheres (the paper's simulation object has nine; their sizes and places are
+    not given), point-sampled at the nodes."""
+    return spheres_phantom(geom, n_spheres=9, seed=seed)
+
+
 def phantom(name: str, geom: Geometry | None = None, seed=1304):
     """Phantom for a named configuration."""
     geom = geom or config(name)
