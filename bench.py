@@ -13,6 +13,7 @@ problem (the operator needs no exchange); the value is the sum over ranks.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -422,6 +423,10 @@ def main():
     ap.add_argument("--pls", action="store_true",
                     help="PLS-TV (FISTA-TV) time to a 1e-3 relative data residual on the 160^3 workload")
     ap.add_argument("--pls-iters", type=int, default=400, help="iteration cap of --pls")
+    ap.add_argument("--lattice-weights", type=int, default=0,
+                    help="1: exact strip-area lattice weights (OAT_LATTICE_EXACT_AREA) in the H / H^T bench")
+    ap.add_argument("--eir", default="", choices=["", "gaussian", "bandpass"],
+                    help="add a synthetic transducer response (H = H^e D G) to the H / H^T bench")
     ap.add_argument("--sph", action="store_true",
                     help="spherical-voxel model H_sph + H_sph^T on the paper's 210 x 210 x 440 grid")
     ap.add_argument("--sph-transducers", type=int, default=0, help="--sph on this many transducers (0: all)")
@@ -454,9 +459,13 @@ def main():
     dev = torch.device("cuda", local)
 
     geom = W.config(args.config)
+    if args.lattice_weights:
+        geom = dataclasses.replace(geom, lattice_weights=args.lattice_weights)
     alpha_np = W.phantom(args.config, geom, seed=1304 + rank)
     y_np = W.random_data(geom, seed=7 + rank)
     plan = oat.Plan(geom, device=local)
+    if args.eir:
+        plan.set_eir(*W.eir_taps(kind=args.eir))
     st = plan.stats(count_grid_points=True)
     pts = st["points_grid"]
     alpha = torch.from_numpy(alpha_np).to(dev)
@@ -549,14 +558,18 @@ def main():
         onchip["l2"]["frac"] = onchip["l2"]["achieved_gbs"] / l2_peak
     onchip["counters_source"] = "profiles/counters.json (ncu, one pass at full size; instructions from the --set full capture)"
 
+    variant = (", exact strip-area lattice weights" if args.lattice_weights else "") + \
+              (f", {args.eir} transducer response (H = H^e D G)" if args.eir else "")
+    if args.lattice_weights:
+        roof["traffic"] = None          # the committed counters are of the uniform-weight kernels
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": [geom.nx, geom.ny, geom.nz], "transducers": geom.n_transducers,
+            "config": {"workload": WORKLOAD + variant, "grid": [geom.nx, geom.ny, geom.nz], "transducers": geom.n_transducers,
                        "samples": geom.n_samples, "points_per_operator": pts,
                        "l2": "inputs larger than L2 (volume 67 MB + data 142 MB per step)",
                        "parallelism": f"replicas x{world}"},
-            "gpu_launches": args.steps * LAUNCHES_PER_STEP,
+            "gpu_launches": args.steps * (LAUNCHES_PER_STEP + (1 if args.eir else 0)),
             "kernel_ms": {"k_brick_gather": g_ms / max(g_n, 1), "k_brick_gather_t": b_ms / max(b_n, 1)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
             "roofline": roof, "onchip": onchip, "clocks": clocks}
