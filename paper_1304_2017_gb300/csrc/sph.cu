@@ -71,6 +71,32 @@ struct SphArgs {
     float sig_hi, sig_lo, df_hi, df_lo, inv2pids;
 };
 
+// Two floats in one 64-bit register, operated on by the packed FP32 instructions of sm_100+
+// (add / mul / fma .rn.f32x2: each rounds like its scalar form, lane by lane).
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pk2(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(f32x2 r, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 // (ph + pl) ~ (ah + al)(bh + bl), the product's rounding error from an FMA, al bl dropped.
 __device__ __forceinline__ void pmul(float ah, float al, float bh, float bl, float &ph, float &pl) {
     ph = __fmul_rn(ah, bh);
@@ -109,11 +135,14 @@ __global__ void __launch_bounds__(kSphFwdThreads, 3) k_sph_fwd(SphArgs a) {
     const long long v0 = (long long)blockIdx.y * a.slab, v1 = min(a.N, v0 + a.slab);
     const int q = task / a.nseg;
     const int l0 = (task - q * a.nseg) * kSphSeg + lane * kSphF;
-    const float4 th = __ldg(a.xd + 2 * q), tl = __ldg(a.xd + 2 * q + 1);
     const float2 f0 = __ldg(a.freq + min(l0, a.L - 1));   // lanes past L compute but never store
-    float Tr[kSphF], Ti[kSphF], Sr[kSphF], Si[kSphF], Cr[kSphF], Ci[kSphF];
+    static_assert(kSphF == 8, "the packed loop pairs frequencies k and k + 4");
+    float Sr[kSphF], Si[kSphF], Cr[kSphF], Ci[kSphF];
+    f32x2 T2r[kSphF / 2], T2i[kSphF / 2];   // (frequency k, frequency k + 4) partial sums
 #pragma unroll
-    for (int k = 0; k < kSphF; ++k) { Tr[k] = Ti[k] = Sr[k] = Si[k] = Cr[k] = Ci[k] = 0.f; }
+    for (int k = 0; k < kSphF; ++k) { Sr[k] = Si[k] = Cr[k] = Ci[k] = 0.f; }
+#pragma unroll
+    for (int k = 0; k < kSphF / 2; ++k) { T2r[k] = 0ull; T2i[k] = 0ull; }
     // this lane's voxel of the current chunk of 32
     int ix, iy, iz;
     {
@@ -122,9 +151,10 @@ __global__ void __launch_bounds__(kSphFwdThreads, 3) k_sph_fwd(SphArgs a) {
     }
     int chunk = 0;
     for (long long base = v0; base < v1; base += 32, ++chunk) {
-        float tauh = 0.f, taul = 0.f, w = 0.f, zr = 1.f, zi = 0.f;
+        float tauh = 0.f, taul = 0.f, w = 0.f, zr = 1.f, zi = 0.f, z4r = 1.f, z4i = 0.f;
         if (base + lane < v1) {
             const float al = __ldg(a.alpha + base + lane);
+            const float4 th = __ldg(a.xd + 2 * q), tl = __ldg(a.xd + 2 * q + 1);   // L1 hits
             float dh, dl;
             sph_dist((float)ix, (float)iy, (float)iz, th, tl, dh, dl);
             pmul(dh, dl, a.sig_hi, a.sig_lo, tauh, taul);
@@ -133,6 +163,9 @@ __global__ void __launch_bounds__(kSphFwdThreads, 3) k_sph_fwd(SphArgs a) {
             pmul(a.df_hi, a.df_lo, tauh, taul, ph, pl);
             sincospif(2.f * pfrac(ph, pl), &s, &c);
             zr = c; zi = -s;                                        // exp(-j 2 pi df tau)
+            pmul(4.f * a.df_hi, 4.f * a.df_lo, tauh, taul, ph, pl);
+            sincospif(2.f * pfrac(ph, pl), &s, &c);
+            z4r = c; z4i = -s;                                      // exp(-j 2 pi 4 df tau)
         }
         ix += 32;
         while (ix >= a.nx) {
@@ -143,28 +176,37 @@ __global__ void __launch_bounds__(kSphFwdThreads, 3) k_sph_fwd(SphArgs a) {
             const float vth = __shfl_sync(0xffffffffu, tauh, j), vtl = __shfl_sync(0xffffffffu, taul, j);
             const float vw = __shfl_sync(0xffffffffu, w, j);
             const float vzr = __shfl_sync(0xffffffffu, zr, j), vzi = __shfl_sync(0xffffffffu, zi, j);
+            const float v4r = __shfl_sync(0xffffffffu, z4r, j), v4i = __shfl_sync(0xffffffffu, z4i, j);
             float ph, pl, s, c;
             pmul(f0.x, f0.y, vth, vtl, ph, pl);
             __sincosf(kTwoPi * pfrac(ph, pl), &s, &c);
-            float er = vw * c, ei = -vw * s;                        // w exp(-j 2 pi f_l0 tau)
+            const float er0 = vw * c, ei0 = -vw * s;                 // w exp(-j 2 pi f_l0 tau)
+            const float er4 = fmaf(er0, v4r, -ei0 * v4i), ei4 = fmaf(er0, v4i, ei0 * v4r);   // ... f_l0+4
+            // frequencies k and k + 4 side by side: one packed rotation serves both
+            f32x2 Er = pk2(er0, er4), Ei = pk2(ei0, ei4);
+            const f32x2 Zr = pk2(vzr, vzr), Zi = pk2(vzi, vzi), NZi = pk2(-vzi, -vzi);
 #pragma unroll
-            for (int k = 0; k < kSphF; ++k) {
-                Tr[k] += er;
-                Ti[k] += ei;
-                if (k + 1 < kSphF) {
-                    const float t = fmaf(er, vzr, -ei * vzi);
-                    ei = fmaf(er, vzi, ei * vzr);
-                    er = t;
+            for (int k = 0; k < kSphF / 2; ++k) {
+                T2r[k] = add2(T2r[k], Er);
+                T2i[k] = add2(T2i[k], Ei);
+                if (k + 1 < kSphF / 2) {
+                    const f32x2 nr = fma2(Er, Zr, mul2(Ei, NZi));
+                    Ei = fma2(Er, Zi, mul2(Ei, Zr));
+                    Er = nr;
                 }
             }
         }
         if ((chunk & 3) == 3 || base + 32 >= v1) {
 #pragma unroll
-            for (int k = 0; k < kSphF; ++k) {
-                float e;
-                two_sum(Sr[k], Tr[k], Sr[k], e); Cr[k] += e;
-                two_sum(Si[k], Ti[k], Si[k], e); Ci[k] += e;
-                Tr[k] = 0.f; Ti[k] = 0.f;
+            for (int k = 0; k < kSphF / 2; ++k) {
+                float lo, hi, e;
+                upk2(T2r[k], lo, hi);
+                two_sum(Sr[k], lo, Sr[k], e); Cr[k] += e;
+                two_sum(Sr[k + 4], hi, Sr[k + 4], e); Cr[k + 4] += e;
+                upk2(T2i[k], lo, hi);
+                two_sum(Si[k], lo, Si[k], e); Ci[k] += e;
+                two_sum(Si[k + 4], hi, Si[k + 4], e); Ci[k + 4] += e;
+                T2r[k] = 0ull; T2i[k] = 0ull;
             }
         }
     }
@@ -200,7 +242,7 @@ __global__ void k_sph_conj(const float2 *__restrict__ u, const double2 *__restri
 }
 
 __global__ void __launch_bounds__(kSphBwdThreads) k_sph_bwd(SphArgs a) {
-    extern __shared__ float2 sv[];   // [qtile][L] rows of v
+    extern __shared__ ulonglong2 sv[];   // [qtile][L]: (v_re, v_re), (-v_im, -v_im) as packed pairs
     const long long n0 = ((long long)blockIdx.x * kSphBwdThreads + threadIdx.x) * 2;
     float px[2], py[2], pz[2];
     bool ok[2];
@@ -219,12 +261,18 @@ __global__ void __launch_bounds__(kSphBwdThreads) k_sph_bwd(SphArgs a) {
         const int nq = min(a.qtile, a.Q - q0);
         __syncthreads();
         const float2 *src = a.v + (size_t)q0 * a.L;
-        for (int i = threadIdx.x; i < nq * a.L; i += blockDim.x) sv[i] = src[i];
+        for (int i = threadIdx.x; i < nq * a.L; i += blockDim.x) {
+            const float2 y = src[i];
+            ulonglong2 t;
+            t.x = pk2(y.x, y.x);
+            t.y = pk2(-y.y, -y.y);
+            sv[i] = t;
+        }
         __syncthreads();
         for (int t = 0; t < nq; ++t) {
             const int q = q0 + t;
             const float4 th = __ldg(a.xd + 2 * q), tl = __ldg(a.xd + 2 * q + 1);
-            float tauh[2], taul[2], w[2], zr[2], zi[2], acc[2];
+            float tauh[2], taul[2], w[2], zr[2], zi[2];
 #pragma unroll
             for (int v = 0; v < 2; ++v) {
                 float dh, dl, ph, pl, s, c;
@@ -234,9 +282,11 @@ __global__ void __launch_bounds__(kSphBwdThreads) k_sph_bwd(SphArgs a) {
                 pmul(a.df_hi, a.df_lo, tauh[v], taul[v], ph, pl);
                 sincospif(2.f * pfrac(ph, pl), &s, &c);
                 zr[v] = c; zi[v] = s;                                 // exp(+j 2 pi df tau)
-                acc[v] = 0.f;
             }
-            const float2 *row = sv + t * a.L;
+            // the two voxels side by side in packed pairs
+            const f32x2 Zr = pk2(zr[0], zr[1]), Zi = pk2(zi[0], zi[1]), NZi = pk2(-zi[0], -zi[1]);
+            f32x2 acc = 0ull;
+            const ulonglong2 *row = sv + t * a.L;
             for (int la = 0; la < a.L; la += kSphAnchor) {
                 const float2 fa = __ldg(a.freq + la);
                 float er[2], ei[2];
@@ -247,39 +297,33 @@ __global__ void __launch_bounds__(kSphBwdThreads) k_sph_bwd(SphArgs a) {
                     __sincosf(kTwoPi * pfrac(ph, pl), &s, &c);
                     er[v] = c; ei[v] = s;                             // exp(+j 2 pi f_la tau)
                 }
+                f32x2 Er = pk2(er[0], er[1]), Ei = pk2(ei[0], ei[1]);
                 const int cnt = min(kSphAnchor, a.L - la);
-                const float2 *rv = row + la;
+                const ulonglong2 *rv = row + la;
+                // Re(v e) = v_re e_re - v_im e_im; e <- e z
+#define OAT_SPH_STEP(Y)                                        \
+    {                                                          \
+        acc = fma2((Y).x, Er, acc);                            \
+        acc = fma2((Y).y, Ei, acc);                            \
+        const f32x2 nr = fma2(Er, Zr, mul2(Ei, NZi));          \
+        Ei = fma2(Er, Zi, mul2(Ei, Zr));                       \
+        Er = nr;                                               \
+    }
                 if (cnt == kSphAnchor) {
 #pragma unroll 8
-                    for (int k = 0; k < kSphAnchor; ++k) {
-                        const float2 y = rv[k];
-#pragma unroll
-                        for (int v = 0; v < 2; ++v) {
-                            acc[v] = fmaf(y.x, er[v], acc[v]);
-                            acc[v] = fmaf(-y.y, ei[v], acc[v]);
-                            const float tt = fmaf(er[v], zr[v], -ei[v] * zi[v]);
-                            ei[v] = fmaf(er[v], zi[v], ei[v] * zr[v]);
-                            er[v] = tt;
-                        }
-                    }
+                    for (int k = 0; k < kSphAnchor; ++k) OAT_SPH_STEP(rv[k])
                 } else {
-                    for (int k = 0; k < cnt; ++k) {
-                        const float2 y = rv[k];
-#pragma unroll
-                        for (int v = 0; v < 2; ++v) {
-                            acc[v] = fmaf(y.x, er[v], acc[v]);
-                            acc[v] = fmaf(-y.y, ei[v], acc[v]);
-                            const float tt = fmaf(er[v], zr[v], -ei[v] * zi[v]);
-                            ei[v] = fmaf(er[v], zi[v], ei[v] * zr[v]);
-                            er[v] = tt;
-                        }
-                    }
+                    for (int k = 0; k < cnt; ++k) OAT_SPH_STEP(rv[k])
                 }
+#undef OAT_SPH_STEP
             }
+            float acc0, acc1;
+            upk2(acc, acc0, acc1);
+            const float accv[2] = {acc0, acc1};
 #pragma unroll
             for (int v = 0; v < 2; ++v) {
                 float e;
-                two_sum(S[v], w[v] * acc[v], S[v], e);
+                two_sum(S[v], w[v] * accv[v], S[v], e);
                 C[v] += e;
             }
         }
@@ -351,7 +395,7 @@ int oat_sph_create(const oat_geometry *geom, int n_freq, double f0_mhz, double d
     for (int d = 0; d < 3; ++d)
         if (!std::isfinite(g.origin_mm[d])) return set_error(OAT_ERR_INVALID_ARG, "oat_sph_create: non-finite origin");
     if (g.n_transducers < 1) return set_error(OAT_ERR_INVALID_ARG, "oat_sph_create: n_transducers must be >= 1");
-    if (n_freq < 1 || n_freq > 25600) return set_error(OAT_ERR_INVALID_ARG, "oat_sph_create: n_freq must be in 1 .. 25600");
+    if (n_freq < 1 || n_freq > 12800) return set_error(OAT_ERR_INVALID_ARG, "oat_sph_create: n_freq must be in 1 .. 12800");
     if (!(f0_mhz > 0.0) || !std::isfinite(f0_mhz) || !(df_mhz >= 0.0) || !std::isfinite(df_mhz) ||
         (n_freq > 1 && !(df_mhz > 0.0)) || !std::isfinite(f0_mhz + (n_freq - 1) * df_mhz))
         return set_error(OAT_ERR_INVALID_ARG, "oat_sph_create: need f0 > 0 and df > 0 (df >= 0 for one frequency)");
@@ -403,8 +447,8 @@ int oat_sph_create(const oat_geometry *geom, int n_freq, double f0_mhz, double d
     p->N = (long long)g.nx * g.ny * g.nz;
     p->Q = Q; p->L = L;
     p->nseg = (L + kSphSeg - 1) / kSphSeg;
-    p->qtile = std::max(1, std::min(64, 32768 / (int)(sizeof(float2) * L)));
-    p->bwd_smem = sizeof(float2) * (size_t)p->qtile * L;
+    p->qtile = std::max(1, std::min(64, 32768 / (int)(sizeof(ulonglong2) * L)));
+    p->bwd_smem = sizeof(ulonglong2) * (size_t)p->qtile * L;
     pair_split(ds / c, p->sig_hi, p->sig_lo);
     pair_split(df_mhz, p->df_hi, p->df_lo);
     p->inv2pids = (float)(1.0 / (2.0 * M_PI * ds));
