@@ -43,7 +43,8 @@ typedef struct oat_sph_s *oat_sph;
  * n_transducers, positions_mm, c_mm_per_us and gruneisen (copied; the time-sampling fields,
  * data_dtype, apply_d and lattice_weights are ignored).  Every transducer must lie at least
  * Delta_s / 2 from every node (outside every spherical voxel).
- * n_freq = L >= 1, f0_mhz > 0, df_mhz >= 0 (> 0 when L > 1); eir: NULL, or a host array of
+ * 1 <= n_freq = L <= 12800 (the adjoint stages transducer rows of v in shared memory),
+ * f0_mhz > 0, df_mhz >= 0 (> 0 when L > 1); eir: NULL, or a host array of
  * [L][2] doubles (re, im) of h_e(f_l), copied.
  * Allocates the transducer table, p0, a [Q][L] complex scratch of the adjoint and the forward's
  * per-slab totals (the voxels are split into slabs so that few transducers still fill the GPU;
