@@ -1,7 +1,8 @@
 // Filtered backprojection (include/oat.h, Sec. III.C, Eq. disfbp): a per-voxel gather over all
 // transducers with two-tap linear interpolation in time and the first difference for dp/dt.
 //
-// k_fbp  one thread block per brick of 8^3 voxels, one voxel per thread.  Transducers come in
+// k_fbp  one thread block per brick of 8^3 voxels, two voxels per thread (z and z + 4, whose
+//        terms run side by side in packed FP32 pairs).  Transducers come in
 //        tiles of 256 through shared memory; for each (brick, transducer) one thread computes,
 //        in float-pair arithmetic, the distance D from the transducer to the brick centre and
 //        the fractional sample index K = D ds / (c dt) - t_min / dt split into an integer and an
@@ -27,8 +28,34 @@
 namespace oat {
 
 constexpr int kFbpB = 8;
-constexpr int kFbpThreads = kFbpB * kFbpB * kFbpB;
-constexpr int kFbpTile = 256;
+constexpr int kFbpThreads = kFbpB * kFbpB * kFbpB / 2;   // two voxels per thread
+constexpr int kFbpTile = 256;                           // transducers per tile, one per thread
+
+// Two floats in one 64-bit register for the packed FP32 instructions of sm_100+
+// (add / mul / fma .rn.f32x2 round like their scalar forms, lane by lane).
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(f32x2 r, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+static_assert(kFbpTile == kFbpThreads, "one transducer set-up per thread and tile");
 
 struct FbpArgs {
     const float4 *xd;            // [2Q]: (T hi, w), (T lo, 0); T in index units from node (0,0,0)
@@ -101,31 +128,56 @@ __device__ __forceinline__ FbpQ fbp_setup(const FbpArgs &a, int q, float cx, flo
     return o;
 }
 
-// One (voxel, transducer) term: sample position from the brick-centre values in Q and the
-// voxel offset (dx, dy, dz), |delta|^2 = dd; returns w_q {..} of Eq. disfbp.  CHECK: treat
-// samples outside 0 .. K-1 as zero (else every sample read is known to be inside).
+// Exact floor of |x| < 2^22 as an integer without a conversion instruction: x + 1.5 2^23 puts
+// the integer in the low mantissa bits (fk is already integral, so the sum is exact).
+__device__ __forceinline__ int int_of_integral(float fk) { return __float_as_int(fk + 12582912.f) - 0x4B400000; }
+
+// The (voxel, transducer) terms of two voxels at offsets (dx, dy, dz0|1) from the brick centre,
+// |delta|^2 = dd0|1 (packed DZ, DD): w_q {..} of Eq. disfbp for each, packed.  Per voxel the
+// operations and their rounding are those of the one-voxel form: distance change dD, sample
+// position k~, two-tap interpolation and first difference.  CHECK: samples outside 0 .. K-1
+// count as zero (else every sample read is known to be inside).
 template <bool CHECK, typename T>
-__device__ __forceinline__ float fbp_term(const FbpQ &Q, const T *row, int K, float dx, float dy, float dz, float dd,
+__device__ __forceinline__ f32x2 fbp_pair(const FbpQ &Q, const T *row, int K, float dx, float dy, f32x2 DZ, f32x2 DD,
                                           float sk) {
-    const float ud = fmaf(Q.uz, dz, fmaf(Q.uy, dy, Q.ux * dx));
-    const float tt = fmaf(2.f * Q.D, ud, dd);
-    const float s2 = fmaf(Q.D, Q.D, tt);
-    const float dD = __fdividef(tt, Q.D + s2 * rsqrtf(s2));          // distance - D
-    const float kf = fmaf(dD, sk, Q.kfrac);
-    const float fk = floorf(kf);
-    const int k = Q.kint + (int)fk;
-    const float wgt = kf - fk;
-    const float tau = fmaf(dD, sk, Q.tau);
-    float p0, p1;
+    const float c = fmaf(Q.uy, dy, Q.ux * dx);
+    const f32x2 UD = fma2(pk2(Q.uz, Q.uz), DZ, pk2(c, c));
+    const float td = 2.f * Q.D;
+    const f32x2 TT = fma2(pk2(td, td), UD, DD);
+    const f32x2 DQ = pk2(Q.D, Q.D);
+    const f32x2 S2 = fma2(DQ, DQ, TT);
+    float s2a, s2b;
+    upk2(S2, s2a, s2b);
+    const f32x2 DEN = add2(DQ, mul2(S2, pk2(rsqrtf(s2a), rsqrtf(s2b))));
+    float dna, dnb;
+    upk2(DEN, dna, dnb);
+    const f32x2 DDD = mul2(TT, pk2(__fdividef(1.f, dna), __fdividef(1.f, dnb)));   // distance - D
+    const f32x2 SK = pk2(sk, sk);
+    const f32x2 KF = fma2(DDD, SK, pk2(Q.kfrac, Q.kfrac));
+    float kfa, kfb;
+    upk2(KF, kfa, kfb);
+    const float fka = floorf(kfa), fkb = floorf(kfb);
+    const int ka = Q.kint + int_of_integral(fka), kb = Q.kint + int_of_integral(fkb);
+    const f32x2 M1 = pk2(-1.f, -1.f);
+    const f32x2 WGT = fma2(pk2(fka, fkb), M1, KF);                 // k~ - k
+    const f32x2 TAU = fma2(DDD, SK, pk2(Q.tau, Q.tau));
+    float p0a, p1a, p0b, p1b;
     if (CHECK) {
-        p0 = (k >= 0 && k < K) ? to_f(row[k]) : 0.f;
-        p1 = (k + 1 >= 0 && k + 1 < K) ? to_f(row[k + 1]) : 0.f;
+        p0a = (ka >= 0 && ka < K) ? to_f(row[ka]) : 0.f;
+        p1a = (ka + 1 >= 0 && ka + 1 < K) ? to_f(row[ka + 1]) : 0.f;
+        p0b = (kb >= 0 && kb < K) ? to_f(row[kb]) : 0.f;
+        p1b = (kb + 1 >= 0 && kb + 1 < K) ? to_f(row[kb + 1]) : 0.f;
     } else {
-        p0 = to_f(row[k]);
-        p1 = to_f(row[k + 1]);
+        p0a = to_f(row[ka]); p1a = to_f(row[ka + 1]);
+        p0b = to_f(row[kb]); p1b = to_f(row[kb + 1]);
     }
-    const float dp = p1 - p0;
-    return Q.w * fmaf(fmaf(wgt, dp, p0), __fdividef(1.f, tau), 0.5f * dp);
+    const f32x2 P0 = pk2(p0a, p0b);
+    const f32x2 DP = fma2(P0, M1, pk2(p1a, p1b));                  // p_{k+1} - p_k
+    float ta, tb;
+    upk2(TAU, ta, tb);
+    const f32x2 IT = pk2(__fdividef(1.f, ta), __fdividef(1.f, tb));
+    const f32x2 BR = fma2(fma2(WGT, DP, P0), IT, mul2(pk2(0.5f, 0.5f), DP));
+    return mul2(pk2(Q.w, Q.w), BR);
 }
 
 template <int DT>
@@ -134,16 +186,17 @@ __global__ void __launch_bounds__(kFbpThreads) k_fbp(FbpArgs a) {
     __shared__ FbpQ tq[kFbpTile];
     const int b = blockIdx.x;
     const int bx = b % a.bx, by = (b / a.bx) % a.by, bz = b / (a.bx * a.by);
-    const int lx = threadIdx.x & 7, ly = (threadIdx.x >> 3) & 7, lz = threadIdx.x >> 6;
+    const int lx = threadIdx.x & 7, ly = (threadIdx.x >> 3) & 7, lz = threadIdx.x >> 6;   // lz 0..3; + 4
     const int ix = bx * kFbpB + lx, iy = by * kFbpB + ly, iz = bz * kFbpB + lz;
     const float cx = bx * kFbpB + 3.5f, cy = by * kFbpB + 3.5f, cz = bz * kFbpB + 3.5f;
-    const float dx = lx - 3.5f, dy = ly - 3.5f, dz = lz - 3.5f;
-    const float dd = dx * dx + dy * dy + dz * dz;
+    const float dx = lx - 3.5f, dy = ly - 3.5f, dz0 = lz - 3.5f, dz1 = lz + 0.5f;
+    const float dxy = dx * dx + dy * dy;
+    const f32x2 DZ = pk2(dz0, dz1), DD = pk2(dxy + dz0 * dz0, dxy + dz1 * dz1);
     const float sk = a.sk_hi;
     // every voxel of the brick is within rb of the centre: its sample index is within rb sk
     // (plus rounding) of the centre's
     const float reach = (3.5f * 1.7320509f + 0.01f) * sk + 1.f;
-    double total = 0.0;
+    double total0 = 0.0, total1 = 0.0;
     for (int q0 = 0; q0 < a.Q; q0 += kFbpTile) {
         const int nt = min(kFbpTile, a.Q - q0);
         __syncthreads();
@@ -156,15 +209,32 @@ __global__ void __launch_bounds__(kFbpThreads) k_fbp(FbpArgs a) {
         }
         const bool all_inside = __syncthreads_and(inside);
         const T *row = (const T *)a.p + (size_t)q0 * a.K;
-        float s = 0.f, e = 0.f;
-        if (all_inside) {
-            for (int t = 0; t < nt; ++t, row += a.K) kadd(s, e, fbp_term<false>(tq[t], row, a.K, dx, dy, dz, dd, sk));
-        } else {
-            for (int t = 0; t < nt; ++t, row += a.K) kadd(s, e, fbp_term<true>(tq[t], row, a.K, dx, dy, dz, dd, sk));
-        }
-        total += (double)s + (double)e;
+        // compensated (Kahan) sums of the tile's terms, both voxels at once
+        f32x2 S = 0ull, C = 0ull;
+        const f32x2 M1 = pk2(-1.f, -1.f);
+#define OAT_FBP_ACC(X)                                 \
+    {                                                  \
+        const f32x2 y_ = fma2(C, M1, (X));             \
+        const f32x2 t_ = add2(S, y_);                  \
+        C = fma2(y_, M1, fma2(S, M1, t_));             \
+        S = t_;                                        \
     }
-    if (ix < a.nx && iy < a.ny && iz < a.nz) a.vol[((size_t)iz * a.ny + iy) * a.nx + ix] = (float)(total * a.scale);
+        if (all_inside) {
+            for (int t = 0; t < nt; ++t, row += a.K) OAT_FBP_ACC((fbp_pair<false>(tq[t], row, a.K, dx, dy, DZ, DD, sk)))
+        } else {
+            for (int t = 0; t < nt; ++t, row += a.K) OAT_FBP_ACC((fbp_pair<true>(tq[t], row, a.K, dx, dy, DZ, DD, sk)))
+        }
+#undef OAT_FBP_ACC
+        float s0, s1, c0, c1;
+        upk2(S, s0, s1);
+        upk2(C, c0, c1);
+        total0 += (double)s0 - (double)c0;
+        total1 += (double)s1 - (double)c1;
+    }
+    if (ix < a.nx && iy < a.ny) {
+        if (iz < a.nz) a.vol[((size_t)iz * a.ny + iy) * a.nx + ix] = (float)(total0 * a.scale);
+        if (iz + 4 < a.nz) a.vol[((size_t)(iz + 4) * a.ny + iy) * a.nx + ix] = (float)(total1 * a.scale);
+    }
 }
 
 int launch_fbp(Plan &p, const void *data, float *vol, cudaStream_t s) {
