@@ -97,3 +97,47 @@ def test_valid_plan_without_gpu_fails_loudly(oat):
     h = ctypes.c_void_p()
     assert oat.lib.oat_plan_create(ctypes.byref(s), 0, ctypes.byref(h)) == oat.OAT_ERR_CUDA
     assert h.value is None
+
+
+def _sph_create(oat, geom, n_freq, f0, df, eir=None):
+    s, pos = _struct(oat, geom)
+    h = ctypes.c_void_p(12345)
+    e = None
+    if eir is not None:
+        e = np.ascontiguousarray(eir, dtype=np.float64)
+    ptr = e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if e is not None else None
+    rc = oat.lib.oat_sph_create(ctypes.byref(s), n_freq, f0, df, ptr, 0, ctypes.byref(h))
+    return rc, h
+
+
+@pytest.mark.parametrize("n_freq,f0,df", [(0, 0.1, 0.1), (4, 0.0, 0.1), (4, -1.0, 0.1), (4, 0.5, 0.0),
+                                          (4, 0.5, -0.1), (4, math.nan, 0.1), (20000, 0.1, 0.1)])
+def test_sph_bad_frequencies_rejected_on_host(oat, n_freq, f0, df):
+    geom = W.make_geometry(6, 0.3, 1, 2, 5.0, 16)
+    rc, h = _sph_create(oat, geom, n_freq, f0, df)
+    assert rc == oat.OAT_ERR_INVALID_ARG, oat.oat_last_error()
+    assert h.value is None
+
+
+def test_sph_host_validation(oat):
+    geom = W.make_geometry(6, 0.3, 1, 2, 5.0, 16, positions_mm=[[0.15, 0.15, 0.15], [5.0, 0, 0]])
+    rc, _ = _sph_create(oat, geom, 4, 0.5, 0.1)                  # transducer 0 inside a voxel sphere
+    assert rc == oat.OAT_ERR_INVALID_ARG and "inside a spherical voxel" in oat.oat_last_error()
+    geom = W.make_geometry(6, 0.3, 1, 2, 5.0, 16)
+    rc, _ = _sph_create(oat, geom, 3, 0.5, 0.1, eir=[1.0, 0.0, math.inf, 0.0, 1.0, 0.0])
+    assert rc == oat.OAT_ERR_INVALID_ARG
+    assert oat.lib.oat_sph_project(None, None, None, None) == oat.OAT_ERR_INVALID_ARG
+    assert oat.lib.oat_sph_backproject(None, None, None, None) == oat.OAT_ERR_INVALID_ARG
+    assert oat.lib.oat_sph_destroy(None) == oat.OAT_OK
+    # no CPU fallback: a valid operator needs the GPU
+    import torch
+    if not torch.cuda.is_available():
+        rc, h = _sph_create(oat, geom, 4, 0.5, 0.1)
+        assert rc == oat.OAT_ERR_CUDA and h.value is None
+
+
+def test_eir_and_fbp_null_args(oat):
+    d = ctypes.POINTER(ctypes.c_double)()
+    assert oat.lib.oat_plan_set_eir(None, d, 0, 0) == oat.OAT_ERR_INVALID_ARG
+    assert oat.lib.oat_plan_set_fbp_weights(None, d) == oat.OAT_ERR_INVALID_ARG
+    assert oat.lib.oat_fbp(None, None, None, None) == oat.OAT_ERR_INVALID_ARG
