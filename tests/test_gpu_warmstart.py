@@ -1,6 +1,6 @@
 """What the trained network gains over plain PLS-TV: the learned warm-start experiment end to
 end at 32^3 (48 training and 6 held-out phantoms, 60 epochs; about a minute on one GB300).
-Zero-start FISTA-TV is the reference and the judge: both runs must reach the 1e-3 relative data
+Zero-start FISTA-TV is the reference and the yardstick: both runs must reach the 1e-3 relative data
 residual, and the warm start must get there in fewer iterations and less GPU time (its network
 and amplitude fit included)."""
 import pytest
