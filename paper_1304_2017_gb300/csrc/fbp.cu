@@ -65,6 +65,7 @@ struct FbpArgs {
     int bx, by;                  // bricks along x and y
     float sk_hi, sk_lo;          // ds / (c dt): index units -> samples, as a float pair
     float t0_hi, t0_lo;          // t_min / dt as a float pair
+    int R, W;                    // staged sample windows: offset R, width W = 2 R + 1
     double scale;                // -1 / (pi Gamma c dt)
 };
 
@@ -125,6 +126,12 @@ __device__ __forceinline__ FbpQ fbp_setup(const FbpArgs &a, int q, float cx, flo
     o.kfrac = __fadd_rn(__fsub_rn(ks, fl), ke);
     o.tau = __fadd_rn(kp, kpe);
     o.w = hi.w;
+    if (!(D0 > 1e-3f) || !(D0 < 1e30f)) {
+        // a transducer at the brick centre (the formula is singular there) or a non-finite
+        // position: no contribution, and finite values so that every sample index stays in
+        // its window
+        o.ux = o.uy = o.uz = 0.f; o.D = 1.f; o.kint = 0; o.kfrac = 0.f; o.tau = 1.f; o.w = 0.f;
+    }
     return o;
 }
 
@@ -136,10 +143,13 @@ __device__ __forceinline__ int int_of_integral(float fk) { return __float_as_int
 // |delta|^2 = dd0|1 (packed DZ, DD): w_q {..} of Eq. disfbp for each, packed.  Per voxel the
 // operations and their rounding are those of the one-voxel form: distance change dD, sample
 // position k~, two-tap interpolation and first difference.  CHECK: samples outside 0 .. K-1
-// count as zero (else every sample read is known to be inside).
-template <bool CHECK, typename T>
+// count as zero (else every sample read is known to be inside).  STAGED: row is the brick's
+// window of this transducer's samples in shared memory, sample kint - R + j at j (zero outside
+// the record), so that sample k reads row[k - kint + R].
+template <int MODE, typename T>
 __device__ __forceinline__ f32x2 fbp_pair(const FbpQ &Q, const T *row, int K, float dx, float dy, f32x2 DZ, f32x2 DD,
-                                          float sk) {
+                                          float sk, int R) {
+    constexpr bool CHECK = MODE == 1, STAGED = MODE == 2;
     const float c = fmaf(Q.uy, dy, Q.ux * dx);
     const f32x2 UD = fma2(pk2(Q.uz, Q.uz), DZ, pk2(c, c));
     const float td = 2.f * Q.D;
@@ -157,7 +167,7 @@ __device__ __forceinline__ f32x2 fbp_pair(const FbpQ &Q, const T *row, int K, fl
     float kfa, kfb;
     upk2(KF, kfa, kfb);
     const float fka = floorf(kfa), fkb = floorf(kfb);
-    const int ka = Q.kint + int_of_integral(fka), kb = Q.kint + int_of_integral(fkb);
+    const int ka = (STAGED ? R : Q.kint) + int_of_integral(fka), kb = (STAGED ? R : Q.kint) + int_of_integral(fkb);
     const f32x2 M1 = pk2(-1.f, -1.f);
     const f32x2 WGT = fma2(pk2(fka, fkb), M1, KF);                 // k~ - k
     const f32x2 TAU = fma2(DDD, SK, pk2(Q.tau, Q.tau));
@@ -180,10 +190,11 @@ __device__ __forceinline__ f32x2 fbp_pair(const FbpQ &Q, const T *row, int K, fl
     return mul2(pk2(Q.w, Q.w), BR);
 }
 
-template <int DT>
+template <int DT, bool STAGED>
 __global__ void __launch_bounds__(kFbpThreads) k_fbp(FbpArgs a) {
     using T = typename DataT<DT>::T;
     __shared__ FbpQ tq[kFbpTile];
+    extern __shared__ float swin[];   // STAGED: [kFbpTile][W] sample windows
     const int b = blockIdx.x;
     const int bx = b % a.bx, by = (b / a.bx) % a.by, bz = b / (a.bx * a.by);
     const int lx = threadIdx.x & 7, ly = (threadIdx.x >> 3) & 7, lz = threadIdx.x >> 6;   // lz 0..3; + 4
@@ -209,6 +220,19 @@ __global__ void __launch_bounds__(kFbpThreads) k_fbp(FbpArgs a) {
         }
         const bool all_inside = __syncthreads_and(inside);
         const T *row = (const T *)a.p + (size_t)q0 * a.K;
+        if (STAGED) {
+            // each warp copies whole windows: rows t = warp, warp + 8, ...; lanes along the row
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            for (int t = warp; t < nt; t += kFbpThreads / 32) {
+                const int k0 = tq[t].kint - a.R;
+                const T *src = row + (size_t)t * a.K;
+                for (int j = lane; j < a.W; j += 32) {
+                    const int k = k0 + j;
+                    swin[t * a.W + j] = (k >= 0 && k < a.K) ? to_f(src[k]) : 0.f;
+                }
+            }
+            __syncthreads();
+        }
         // compensated (Kahan) sums of the tile's terms, both voxels at once
         f32x2 S = 0ull, C = 0ull;
         const f32x2 M1 = pk2(-1.f, -1.f);
@@ -219,10 +243,13 @@ __global__ void __launch_bounds__(kFbpThreads) k_fbp(FbpArgs a) {
         C = fma2(y_, M1, fma2(S, M1, t_));             \
         S = t_;                                        \
     }
-        if (all_inside) {
-            for (int t = 0; t < nt; ++t, row += a.K) OAT_FBP_ACC((fbp_pair<false>(tq[t], row, a.K, dx, dy, DZ, DD, sk)))
+        if (STAGED) {
+            for (int t = 0; t < nt; ++t)
+                OAT_FBP_ACC((fbp_pair<2>(tq[t], swin + t * a.W, a.K, dx, dy, DZ, DD, sk, a.R)))
+        } else if (all_inside) {
+            for (int t = 0; t < nt; ++t, row += a.K) OAT_FBP_ACC((fbp_pair<0>(tq[t], row, a.K, dx, dy, DZ, DD, sk, 0)))
         } else {
-            for (int t = 0; t < nt; ++t, row += a.K) OAT_FBP_ACC((fbp_pair<true>(tq[t], row, a.K, dx, dy, DZ, DD, sk)))
+            for (int t = 0; t < nt; ++t, row += a.K) OAT_FBP_ACC((fbp_pair<1>(tq[t], row, a.K, dx, dy, DZ, DD, sk, 0)))
         }
 #undef OAT_FBP_ACC
         float s0, s1, c0, c1;
@@ -248,13 +275,34 @@ int launch_fbp(Plan &p, const void *data, float *vol, cudaStream_t s) {
     a.t0_hi = (float)t0; a.t0_lo = (float)(t0 - (double)a.t0_hi);
     a.scale = -1.0 / (M_PI * p.g.gruneisen * p.g.c_mm_per_us * p.dt);
     const unsigned blocks = (unsigned)((size_t)a.bx * a.by * bz);
+    // every voxel of a brick lies within 3.5 sqrt(3) grid units of its centre, so its sample
+    // index is within that times sk of the centre's (the kernel's reach, plus a margin): the
+    // samples any brick reads for one transducer lie in kint - R .. kint + R
+    const double reach = (3.5 * std::sqrt(3.0) + 0.01) * sk + 1.0;
+    a.R = (int)std::ceil(reach) + 1;
+    a.W = 2 * a.R + 1;
+    const size_t win_bytes = sizeof(float) * (size_t)kFbpTile * a.W;
+    bool staged = win_bytes <= 96 * 1024;   // else the direct (L2) reads
+    if (staged) {
+        cudaError_t ea = cudaSuccess;
+        switch (p.g.data_dtype) {
+            case OAT_F32: ea = cudaFuncSetAttribute(k_fbp<OAT_F32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_bytes); break;
+            case OAT_F16: ea = cudaFuncSetAttribute(k_fbp<OAT_F16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_bytes); break;
+            default: ea = cudaFuncSetAttribute(k_fbp<OAT_BF16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_bytes); break;
+        }
+        if (ea != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_fbp: cudaFuncSetAttribute: ") + cudaGetErrorString(ea));
+    }
     const bool prof = p.profiling && p.ev_used[2] + 2 <= (int)p.ev[2].size();
     if (prof) cudaEventRecord(p.ev[2][p.ev_used[2]], s);
+    const size_t sm = staged ? win_bytes : 0;
+#define OAT_FBP_LAUNCH(DTV)                                                                     \
+    (staged ? k_fbp<DTV, true><<<blocks, kFbpThreads, sm, s>>>(a) : k_fbp<DTV, false><<<blocks, kFbpThreads, 0, s>>>(a))
     switch (p.g.data_dtype) {
-        case OAT_F32: k_fbp<OAT_F32><<<blocks, kFbpThreads, 0, s>>>(a); break;
-        case OAT_F16: k_fbp<OAT_F16><<<blocks, kFbpThreads, 0, s>>>(a); break;
-        default: k_fbp<OAT_BF16><<<blocks, kFbpThreads, 0, s>>>(a); break;
+        case OAT_F32: OAT_FBP_LAUNCH(OAT_F32); break;
+        case OAT_F16: OAT_FBP_LAUNCH(OAT_F16); break;
+        default: OAT_FBP_LAUNCH(OAT_BF16); break;
     }
+#undef OAT_FBP_LAUNCH
     if (prof) { cudaEventRecord(p.ev[2][p.ev_used[2] + 1], s); p.ev_used[2] += 2; }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? OAT_OK : set_error(OAT_ERR_CUDA, std::string("oat_fbp: k_fbp: ") + cudaGetErrorString(e));

@@ -91,6 +91,9 @@ CASES = {
     "tmin0": (lambda: W.make_geometry(12, 0.29, 2, 4, 6.07, 120, t_min_us=0.0), "smooth"),
     "window_cut": (lambda: W.make_geometry(14, 0.31, 3, 4, 8.11, 30), "smooth"),
     "physical": (lambda: W.make_geometry(20, 0.251, 6, 8, 8.03, 160), "forward"),
+    # coarse grid at 40 MHz: about 16 samples per grid spacing, so a brick's sample windows are
+    # too wide to stage in shared memory and the kernel reads the data directly
+    "coarse_direct": (lambda: W.make_geometry(10, 0.61, 3, 4, 9.13, 400, fs_mhz=40.0), "smooth"),
 }
 
 
@@ -100,7 +103,7 @@ def test_fbp_matches_reference(env, case, dtype):
     torch, oat = env
     make, kind = CASES[case]
     geom = make()
-    n_r = {"ragged": 3, "tmin0": 2, "window_cut": 3, "physical": 6}[case]
+    n_r = {"ragged": 3, "tmin0": 2, "window_cut": 3, "physical": 6, "coarse_direct": 3}[case]
     n_v = geom.n_transducers // n_r
     w = F.arc_weights(geom.positions_mm, n_r, n_v)
     p = _data(geom, kind, 11)
