@@ -124,7 +124,9 @@ int oat_plan_destroy(oat_plan plan);
  * u = H alpha (or G alpha when apply_d = 0)  -- Eqs. dis_srt and dis_g2p.
  *   d_vol   device, float32 [nz][ny][nx], read only
  *   d_data  device, [Q][K] of data_dtype, fully overwritten
- * D rows 0 and K-1 are zero; a D term whose tau_k = t_k / dt is <= 0 is zero.
+ * D rows 0 and K-1 are zero; a D term whose tau_k = t_k / dt is <= 0 is zero.  The lattice
+ * points carry the plan's lattice_weights; with a transducer response set (oat_plan_set_eir)
+ * the result is H^e D G alpha (H^e G alpha without D).
  * Errors: OAT_ERR_INVALID_ARG (NULL plan or pointer, pointer not 16-byte aligned),
  *         OAT_ERR_CUDA (launch failure).
  */
@@ -132,8 +134,9 @@ int oat_project(oat_plan plan, const float *d_vol, void *d_data, void *stream);
 
 /*
  * alpha' = H^T y (or G^T y when apply_d = 0)  -- the adjoints of Sec. II.B.  Exact transpose
- * of oat_project: the same FP32 lattice points, the same interpolation weights; D^T is the
- * exact transpose of D including its zero boundary rows.  Computed brick by brick: each brick of
+ * of oat_project: the same FP32 lattice points, the same interpolation and lattice weights; D^T
+ * is the exact transpose of D including its zero boundary rows; with a transducer response set,
+ * H^e^T is applied first.  Computed brick by brick: each brick of
  * voxels sums the weighted lattice points that fall in its cells as exact fixed-point integers,
  * so there are no floating-point atomics and the result does not depend on execution order.
  *   d_data  device, [Q][K] of data_dtype, read only

@@ -18,6 +18,9 @@
 //                   are folded into the volume's 64-bit accumulator (integer global atomics: the
 //                   nodes on brick faces are shared with neighbouring bricks).
 // k_finish_t        alpha'_n = sum_n / scale * Delta_s^2 as float32: every voxel written once.
+// AREA instances scale each point's g' by its ring's exact-strip-area weight factor (carried
+// in a per-warp queue beside the points).  With a transducer response set, eir.cu's k_eir_t
+// first forms z = H^e^T y and the gather reads z as float32 data.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 

@@ -7,6 +7,9 @@
 //                  float32 / float16 / bfloat16 at the end.
 // k_absmax         max |x| of a buffer (the fixed-point units of both directions).
 // k_brick_gather<COUNT>  lattice points whose stencil touches the grid (oat_plan_query).
+// k_brick_gather<AREA>   the same gather with each point's value scaled by its ring's
+//                  exact-strip-area weight factor (OAT_LATTICE_EXACT_AREA).
+// With a transducer response set, eir.cu's k_apply_d_eir replaces k_apply_d_fix.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
