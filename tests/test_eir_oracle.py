@@ -4,6 +4,7 @@ adjoint identity."""
 import numpy as np
 
 from oracle import eir as E
+from eir_conv import conv_rows, corr_rows
 
 
 def test_identity_and_delay_kernels():
@@ -43,3 +44,12 @@ def test_adjoint_identity():
         lhs = float((E.Heir(p, h, m0) * u).sum())
         rhs = float((p * E.Heir_t(u, h, m0)).sum())
         assert abs(lhs - rhs) <= 1e-13 * np.linalg.norm(p) * np.linalg.norm(u)
+
+
+def test_long_record_helpers_match_the_reference():
+    """The convolution helpers of the long-record test equal the reference on a short record."""
+    rng = np.random.default_rng(9)
+    p = rng.standard_normal((2, 50)); h = rng.standard_normal(13)
+    for m0 in (-20, -7, 0, 4):
+        assert np.allclose(conv_rows(p, h, m0), E.Heir(p, h, m0), rtol=1e-12, atol=1e-12)
+        assert np.allclose(corr_rows(p, h, m0), E.Heir_t(p, h, m0), rtol=1e-12, atol=1e-12)

@@ -9,6 +9,7 @@ import pytest
 
 import oracle
 from oracle import eir as E
+from eir_conv import conv_rows, corr_rows
 from paper_1304_2017_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -141,6 +142,23 @@ def test_eir_bad_args(env):
             plan.set_eir(np.ones(40000), 0)
     finally:
         plan.close()
+
+
+def test_eir_long_record_near_the_shared_memory_bound(env):
+    """K = 20,000 samples at 20 MHz with 7,000 taps: (K + taps) doubles = 216 KB of a block's shared memory
+    (the bound is the device's opt-in maximum, 227 KB on GB300)."""
+    torch, oat = env
+    geom = W.make_geometry(6, 0.5, 1, 2, 6.0, 20000, t_min_us=0.0)
+    rng = np.random.default_rng(8)
+    h = rng.standard_normal(7000) / 7000.0
+    m0 = -3500
+    alpha = W.spheres_phantom(geom, 2, seed=3, r_range=(0.4, 0.9))
+    y = W.random_data(geom, seed=4)
+    u, a, yq = run(env, geom, h, m0, alpha, y)
+    errs = (rel(u, conv_rows(oracle.H(geom, alpha), h, m0)),
+            rel(a, oracle.Ht(geom, corr_rows(yq.astype(np.float64), h, m0))))
+    print("eir K = 20000", errs)
+    assert max(errs) <= TOL, errs
 
 
 def test_eir_full_size(env):

@@ -93,6 +93,30 @@ def test_sph_with_eir_and_bad_args(env):
         assert e.value.code == oat.OAT_ERR_INVALID_ARG
 
 
+def test_sph_maximum_frequency_count(env):
+    """L = 12,800, the largest the adjoint's shared-memory staging takes (one transducer row of
+    packed values per tile, 200 KB): both directions against the reference on a small grid."""
+    torch, oat = env
+    geom = W.make_geometry((4, 3, 5), 0.3, 1, 2, 5.0, 16)
+    L, f0, df = 12800, 0.01, 5.0 / 12800
+    rng = np.random.default_rng(21)
+    alpha = rng.standard_normal(geom.vol_shape).astype(np.float32)
+    u_in = (rng.standard_normal((geom.n_transducers, L)) + 1j * rng.standard_normal((geom.n_transducers, L)))
+    u_in = u_in.astype(np.complex64)
+    op = oat.SphOp(geom, L, f0, df)
+    try:
+        u = op.project(torch.from_numpy(alpha).cuda()).cpu().numpy()
+        a = op.backproject(torch.from_numpy(u_in).cuda()).cpu().numpy()
+    finally:
+        op.close()
+    freqs = f0 + df * np.arange(L)
+    errs = (rel(u, S.H_sph(geom, alpha, freqs)), rel(a, S.H_sph_t(geom, u_in, freqs)))
+    print("sph L = 12800", errs)
+    assert max(errs) <= TOL, errs
+    with pytest.raises(oat.OatError):
+        oat.SphOp(geom, 12801, f0, df)
+
+
 def test_sph_full_size_sampled(env):
     """The paper's simulation scale: 210 x 210 x 440 nodes at 0.14 mm, 64 rings x 90 views on 65 mm,
     511 frequencies in (0, 5] MHz.  Sampled outputs against the reference: u at 3 transducers x 4
