@@ -33,7 +33,6 @@ WORKLOAD = "256^3 @ 0.2 mm, 200 ellipsoids, 128 rings x 180 views (23040 transdu
 # FP32 operations charged to one interpolated sample: lattice point
 # 6 FMA (12), floor 3, fraction 3, 7 lerps (7 sub + 7 FMA = 21), accumulate 1.
 FLOP_PER_SAMPLE = 40.0
-N_SM = 152
 # kernels of this library per step: k_absmax, k_brick_gather, k_apply_d_fix (H); k_absmax,
 # k_brick_gather_t, k_finish_t (H^T)
 LAUNCHES_PER_STEP = 6
@@ -48,6 +47,19 @@ def _peaks():
         return mp, "measured"
     except OSError:
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _sm_count(dev=0):
+    """SM count of the device (the FP32 peak's unit count)."""
+    import torch
+    return torch.cuda.get_device_properties(dev).multi_processor_count
+
+
+def _config(geom, world=1):
+    """The workload's identity, the same dict in both arms."""
+    return {"workload": WORKLOAD, "grid": [geom.nx, geom.ny, geom.nz], "transducers": geom.n_transducers,
+            "samples": geom.n_samples, "l2": "inputs larger than L2 (volume 67 MB + data 142 MB per step)",
+            "parallelism": f"replicas x{world}"}
 
 
 def _counters():
@@ -191,7 +203,10 @@ def run_reference(args):
     geom = W.config("c2")
     alpha = W.phantom("c2", geom)
     y = W.random_data(geom, seed=7)
-    n_x = int(os.environ.get("OAT_REF_XDCR", "8"))
+    # one transducer per host thread at least, so that every core works (H parallelises over
+    # transducers, H^T over transducers too, capped at their number)
+    threads = oracle.max_threads()
+    n_x = int(os.environ.get("OAT_REF_XDCR", str(max(16, threads))))
     qs = np.linspace(0, geom.n_transducers - 1, n_x).round().astype(int)
     sub = geom.subset(qs)
     pts = oracle.count_points(sub)[1]
@@ -206,12 +221,14 @@ def run_reference(args):
         oracle.Ht(sub, ys)
     dt = (time.perf_counter() - t0) / max(args.steps, 1)
     value = 2.0 * pts / dt
+    cores = min(threads, n_x)
+    sample = (f"{n_x} of {geom.n_transducers} transducers (evenly spaced) per step, full grid and time window, "
+              f"one H + one H^T in FP64 on {cores} host threads")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": f"{n_x} evenly spaced transducers per step"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-                             "sample": f"{n_x} of {geom.n_transducers} transducers, full grid and window"},
+            "config": _config(geom),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -344,8 +361,9 @@ def run_sph(args):
     terms = float(geom.n_voxels) * geom.n_transducers * L
     peaks, src = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = {"tflops": N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12,
-            "source": f"{src}: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz"}
+    n_sm = _sm_count(dev)
+    peak = {"tflops": n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12,
+            "source": f"{src} clock: {n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz"}
     dom, dom_t = ("k_sph_bwd (H_sph^T)", t_bwd) if t_bwd >= t_fwd else ("k_sph_fwd (H_sph)", t_fwd)
     line = {"metric": "H_sph+H_sph^T complex terms/s (spherical-voxel model, Eqs. dis_sph and sphbwd)",
             "value": 2 * terms / (t_fwd + t_bwd), "unit": "terms/s", "ms_per_step": (t_fwd + t_bwd) * 1e3,
@@ -414,7 +432,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--learned", action="store_true",
                     help="learned warm start: train the U-Net on PLS-TV targets, compare time to a 1e-3 residual")
     ap.add_argument("--learned-args", default="", help="k=v,... overrides for warmstart.run (e.g. n_train=8)")
@@ -534,20 +552,21 @@ def main():
     dom_ms, dom_name = (b_ms / max(b_n, 1), "k_brick_gather_t (H^T)") if b_ms >= g_ms else (g_ms / max(g_n, 1), "k_brick_gather (H)")
     peaks, src = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    n_sm = _sm_count(dev)
+    peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = FLOP_PER_SAMPLE * pts / (dom_ms * 1e-3) / 1e12
     counters = _counters().get(dom_name.split()[0], {})
     traffic = counters.get("dram_bytes_per_launch")
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": achieved / peak_tflops, "traffic": traffic, "kernel": dom_name,
-            "kernel_ms": dom_ms, "peak_source": f"{src}: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
+            "kernel_ms": dom_ms, "peak_source": f"{src} clock: {n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
             "flop_per_sample": FLOP_PER_SAMPLE}
     # on-chip bounds of the dominant kernel: instruction issue (4 warp instructions per clock per
     # SM) at its measured instruction count, and L2 bytes against a measured L2 copy bandwidth
     onchip = {}
     ips = counters.get("warp_instructions_per_sample")
     if ips:
-        bound = N_SM * 4 * sm_max * 1e6 / ips
+        bound = n_sm * 4 * sm_max * 1e6 / ips
         onchip["issue"] = {"warp_instructions_per_sample": ips, "bound_samples_per_s": bound,
                            "achieved_samples_per_s": pts / (dom_ms * 1e-3), "frac": pts / (dom_ms * 1e-3) / bound}
     l2_peak = l2_read_gbs(dev)
@@ -565,10 +584,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD + variant, "grid": [geom.nx, geom.ny, geom.nz], "transducers": geom.n_transducers,
-                       "samples": geom.n_samples, "points_per_operator": pts,
-                       "l2": "inputs larger than L2 (volume 67 MB + data 142 MB per step)",
-                       "parallelism": f"replicas x{world}"},
+            "config": dict(_config(geom, world), workload=WORKLOAD + variant),
+            "points_per_operator": pts,
             "gpu_launches": args.steps * (LAUNCHES_PER_STEP + (1 if args.eir else 0)),
             "kernel_ms": {"k_brick_gather": g_ms / max(g_n, 1), "k_brick_gather_t": b_ms / max(b_n, 1)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},

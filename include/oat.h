@@ -139,6 +139,10 @@ int oat_project(oat_plan plan, const float *d_vol, void *d_data, void *stream);
  * H^e^T is applied first.  Computed brick by brick: each brick of
  * voxels sums the weighted lattice points that fall in its cells as exact fixed-point integers,
  * so there are no floating-point atomics and the result does not depend on execution order.
+ * The fixed-point unit adapts to the data: transducers are taken in passes whose largest
+ * |D^T y| lie within a factor 2^8 of each other, each pass rounds its contributions to 30 bits
+ * of its own largest |D^T y| and folds, exactly, into a finer 64-bit per-voxel unit; a spike or
+ * an outlier transducer row therefore costs no precision in the other rows.
  *   d_data  device, [Q][K] of data_dtype, read only
  *   d_vol   device, float32 [nz][ny][nx], fully overwritten
  * Errors: as oat_project.
@@ -147,15 +151,18 @@ int oat_backproject(oat_plan plan, const void *d_data, float *d_vol, void *strea
 
 /*
  * alpha' = H^T y exactly as oat_backproject, for callers that cannot allocate device memory at
- * the time of the call: the backprojector's scratch (a 64-bit accumulator per voxel and one
- * max|y| word) is taken from an array of this library in static device memory instead of the
- * plan's scratch, and the call allocates nothing (no cudaMalloc or cudaFree, no allocating
- * library call).  This entry point has no counterpart in the paper.
+ * the time of the call: the backprojector's per-voxel scratch (a 64-bit accumulator per voxel and
+ * one max|D^T y| word) is taken from an array of this library in static device memory instead of
+ * the plan's scratch, and the call allocates nothing (no cudaMalloc or cudaFree, no allocating
+ * library call).  The per-transducer maxima of |D^T y| still use the plan's own scratch, which
+ * oat_plan_create allocated.  This entry point has no counterpart in the paper.
  *   Limit: nx * ny * nz <= 2,097,152 voxels (the array holds 16 MiB + 256 bytes on every GPU
  *          that loads the library, until the process exits); larger volumes return
  *          OAT_ERR_INVALID_ARG.
  *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- *   that device current; make that first call before any stream capture.
+ *   that device current and keeps it for the life of the process; make that first call before
+ *   any stream capture.  The kept address does not survive cudaDeviceReset on that device: do
+ *   not call this entry point again in a process that has reset the device.
  *   All calls share the array and each clears what it needs at its start, so two calls whose
  *   work overlaps on the GPU (on different streams, or from different plans) race and give wrong
  *   results; order them.

@@ -43,6 +43,17 @@ def arc_weights(positions_mm, n_rings, n_views):
     return rs * (math.pi / n_rings) * (2.0 * math.pi / n_views) * np.sin(theta)
 
 
+def sample_positions(geom, nodes, transducers):
+    """k~ = (|r_q - r_n| / c - t_min) / dt (Eq. linearint) in FP64 for (node, transducer) pairs:
+    nodes (n, 3) integer (ix, iy, iz), transducers (n,) integer."""
+    nd = np.asarray(nodes, np.int64).reshape(-1, 3)
+    qs = np.asarray(transducers, np.int64).reshape(-1)
+    o = np.asarray(geom.origin_mm, np.float64)
+    r = o[None, :] + geom.spacing_mm * nd.astype(np.float64)
+    d = np.sqrt(((r - geom.positions_mm[qs]) ** 2).sum(axis=1))
+    return (d / geom.c_mm_per_us - geom.t_min_us) / (1.0 / geom.fs_mhz)
+
+
 def fbp(geom, p, weights, nodes=None, absolute=False, ambiguity=0.0):
     """alpha_fbp from data p [Q][K] (Eq. disfbp): on the whole node grid of `geom` as
     (nz, ny, nx), or at the nodes given as (ix, iy, iz) triples (a 1-D array).

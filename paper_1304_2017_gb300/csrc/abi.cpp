@@ -3,9 +3,11 @@
 // plan builder (plan.cpp).
 #include <cstdint>
 #include <cmath>
+#include <mutex>
 #include <string>
 
 #include "oat_internal.h"
+#include "../../include/oat_probe.h"
 
 namespace oat {
 
@@ -17,6 +19,23 @@ static thread_local std::string g_last_error;
 int set_error(int code, const std::string &msg) {
     g_last_error = msg;
     return code;
+}
+
+int current_sm_count() {
+    static std::mutex mu;
+    static int cache[256] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) { cudaGetLastError(); return 1; }
+    std::lock_guard<std::mutex> lock(mu);
+    if (cache[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+            cudaGetLastError();
+            return 1;
+        }
+        cache[dev] = n;
+    }
+    return cache[dev];
 }
 
 namespace {
@@ -119,6 +138,17 @@ int oat_fbp(oat_plan plan, const void *d_data, float *d_vol, void *stream) {
     DeviceGuard dg(p->device);
     if (dg.err != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_fbp: ") + cudaGetErrorString(dg.err));
     return launch_fbp(*p, d_data, d_vol, (cudaStream_t)stream);
+}
+
+int oat_fbp_sample_positions(oat_plan plan, const int *d_nodes, const int *d_transducers, int n, double *d_out,
+                             void *stream) {
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || n < 0 || (n > 0 && (!d_nodes || !d_transducers || !d_out)))
+        return set_error(OAT_ERR_INVALID_ARG, "oat_fbp_sample_positions: NULL plan or buffer, or n < 0");
+    DeviceGuard dg(p->device);
+    if (dg.err != cudaSuccess)
+        return set_error(OAT_ERR_CUDA, std::string("oat_fbp_sample_positions: ") + cudaGetErrorString(dg.err));
+    return launch_fbp_kpos(*p, d_nodes, d_transducers, n, d_out, (cudaStream_t)stream);
 }
 
 int oat_plan_set_eir(oat_plan plan, const double *h, int n_taps, int first_index) {

@@ -11,13 +11,21 @@
 //                   the brick (brick.cuh), evaluates each with the lattice-point functions shared
 //                   with the projector (oat_internal.h), and for the points whose cell lies in
 //                   the brick adds the
-//                   eight weights w_c g'_{q,k}, rounded to a fixed-point unit chosen from max|y|,
-//                   to the brick's (kBA+1)^3 node sums with 32-bit integer shared-memory atomics.
+//                   eight weights w_c g'_{q,k}, rounded to the pass's fixed-point unit, to the
+//                   brick's (kBA+1)^3 node sums with 32-bit integer shared-memory atomics.
 //                   Integer addition is exact and associative, so the sums do not depend on the
 //                   order of the points.  After each bounded pass of transducers the node sums
-//                   are folded into the volume's 64-bit accumulator (integer global atomics: the
-//                   nodes on brick faces are shared with neighbouring bricks).
-// k_finish_t        alpha'_n = sum_n / scale * Delta_s^2 as float32: every voxel written once.
+//                   are folded, exactly, into the volume's 64-bit accumulator (integer global
+//                   atomics: the nodes on brick faces are shared with neighbouring bricks).
+// Fixed-point units.  k_gprime_rowmax first takes, per transducer q, M_q = max |g'_{q,k}| over
+// the samples whose shells can reach the grid.  A pass over transducers Q_p uses the unit
+// 2^-e_p with e_p chosen so that every contribution |w g'| <= max_{q in Q_p} M_q maps to at most
+// 2^30 units: each pass keeps 30 bits relative to its own data, so a spike or a
+// wide-dynamic-range record in one pass costs no precision in the others.  The volume
+// accumulator's unit 2^-e_g is finer (e_g >= e_p: a pass folds in by an exact left shift); it
+// is chosen from the largest M_q and the plan's bound on the contributions one node can
+// receive, so that no 64-bit sum can overflow.
+// k_finish_t        alpha'_n = sum_n 2^-e_g Delta_s^2 as float32: every voxel written once.
 // AREA instances scale each point's g' by its ring's exact-strip-area weight factor (carried
 // in a per-warp queue beside the points).  With a transducer response set, eir.cu's k_eir_t
 // first forms z = H^e^T y and the gather reads z as float32 data.
@@ -33,21 +41,35 @@ namespace oat {
 
 constexpr int kAdjThreads = 1024;
 
-__global__ void k_absmax(const void *__restrict__ x, size_t n, int dtype, unsigned int *out);
-
 struct AdjArgs {
     DevTables t;
     const void *y;
     unsigned long long *vacc;     // [N] fixed-point node sums
-    const unsigned int *amax;     // bits of max |y|
+    const float *rowmax;          // [Q] M_q = max |g'_{q,k}| over the shells that reach the grid
+    const unsigned int *amax;     // bits of max_q M_q
     int nx, ny, nz, K, Q;
     int nb[3], bs[3];
     int qchunk, kspan, qpass;
     float O[3], O_lo[3];
     float R0, dR;
-    float gscale;                 // max |g'| / max |y|
+    float wfac;                   // bound of a point's lattice-weight factor (1 with uniform weights)
+    int fbits;                    // the volume accumulator holds max M_q wfac as 2^fbits units at most
     int apply_d;
 };
+
+// Exponent e such that |x| 2^e <= 2^bits for every |x| <= bound (bound = m 2^ex, m in [0.5, 1),
+// e = bits - ex); 0 when bound is zero or not finite.
+__host__ __device__ __forceinline__ int pow2_exp(double bound, int bits) {
+    if (!(bound > 0.0) || !(bound < 1e300)) return 0;
+    int ex;
+    frexp(bound, &ex);
+    return bits - ex;
+}
+
+// Exponent of the volume accumulator's unit: every contribution, in that unit, is at most 2^fbits.
+__device__ __forceinline__ int volume_exp(const unsigned int *amax, float wfac, int fbits) {
+    return pow2_exp((double)__uint_as_float(*amax) * (double)wfac, fbits);
+}
 
 template <int DT>
 __device__ __forceinline__ float load_data(const void *p, size_t i) {
@@ -66,6 +88,32 @@ __device__ __forceinline__ float gprime(const AdjArgs &a, int q, int k) {
     float lo = (k - 1 >= 1 && k - 1 <= a.K - 2) ? load_data<DT>(a.y, base + k - 1) : 0.f;
     float hi = (k + 1 >= 1 && k + 1 <= a.K - 2) ? load_data<DT>(a.y, base + k + 1) : 0.f;
     return w * (lo - hi);
+}
+
+// M_q = max |g'_{q,k}| over the samples kr[q].x .. kr[q].y (the shells that can reach the grid,
+// from the plan), computed with the gather's own gprime so that every g' the gather uses is
+// bounded by it; max_q M_q into *amax (NaN wins: its unit then becomes 1).  One warp per row.
+template <int DT>
+__global__ void k_gprime_rowmax(AdjArgs a, const int2 *__restrict__ kr, float *rowmax, unsigned int *amax) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    float wmax = 0.f;
+    for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < a.Q; q += warps) {
+        const int2 r = __ldg(kr + q);
+        float m = 0.f;
+        for (int k = r.x + lane; k <= r.y; k += 32) {
+            const float v = fabsf(gprime<DT>(a, q, k));
+            m = (v > m || v != v) ? v : m;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float w = __shfl_xor_sync(0xffffffffu, m, o);
+            m = (w > m || w != w) ? w : m;
+        }
+        if (lane == 0) rowmax[q] = m;
+        wmax = (m > wmax || m != m) ? m : wmax;
+    }
+    if (lane == 0) atomicMax(amax, __float_as_uint(wmax));
 }
 
 // Node sums of one pass live in shared memory as two 32-bit integer halves of the
@@ -146,8 +194,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
     }
     __syncthreads();
     const float &rb = rbs[0], &rb2 = rbs[1];
-    // contributions |w g'| <= max|g'| map to at most 2^30 units
-    const float scale = (float)pow2_scale((double)__uint_as_float(*a.amax) * (double)a.gscale, 30);
+    __shared__ struct { float scale; int qe; long long fold; } s_pass;   // the current pass: unit, end
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     SegSlot *ws = slots + warp * 32;
     float4 *wq = queues + warp * kQueue;
@@ -156,8 +203,58 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
     float *wg = s_wg[warp];
     const unsigned lt_mask = (1u << lane) - 1u;
 
-    for (int qp = q0; qp < q1; qp += a.qpass) {
-        const int qe = min(q1, qp + a.qpass);
+    int qe = q0;   // end of the current pass, read from s_pass right after the pass's first barrier
+    for (int qp = q0; qp < q1; qp = qe) {
+        // the pass: at most qpass transducers from qp on, ended early before a transducer whose
+        // max |g'| would spread the pass's maxima by more than 2^8, so that every transducer's
+        // contributions keep at least 22 bits of its own maximum (a spike or an outlier row gets
+        // a pass of its own).  Its unit 2^-ep: contributions |w g'| <= max_{q in pass} M_q wfac
+        // map to at most 2^30 units; never finer than the volume accumulator's unit 2^-eg, so that
+        // the pass folds in exactly (ep in [-113, 126], so 2^ep is a normal float).
+        if (warp == 0) {
+            const int n = min(a.qpass, q1 - qp);
+            float hi = 0.f, lo = __int_as_float(0x7f800000);   // running max and least positive max
+            int cut = n;
+            for (int base = 0; base < n; base += 32) {
+                const int i = base + lane;
+                float v = i < n ? __ldg(a.rowmax + qp + i) : 0.f;
+                if (v != v) v = __int_as_float(0x7f800000);   // NaN rows: alone in their pass
+                float vh = v, vl = v > 0.f ? v : __int_as_float(0x7f800000);
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const float th = __shfl_up_sync(0xffffffffu, vh, o), tl = __shfl_up_sync(0xffffffffu, vl, o);
+                    if (lane >= o) { vh = fmaxf(vh, th); vl = fminf(vl, tl); }
+                }
+                vh = fmaxf(vh, hi);
+                vl = fminf(vl, lo);
+                const unsigned bad = __ballot_sync(0xffffffffu, i < n && vh > 256.f * vl);
+                if (bad) {
+                    cut = max(1, base + __ffs(bad) - 1);
+                    break;
+                }
+                hi = __shfl_sync(0xffffffffu, vh, 31);
+                lo = __shfl_sync(0xffffffffu, vl, 31);
+            }
+            float m = 0.f;
+            for (int q = qp + lane; q < qp + cut; q += 32) {
+                const float v = __ldg(a.rowmax + q);
+                m = (v > m || v != v) ? v : m;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float w = __shfl_xor_sync(0xffffffffu, m, o);
+                m = (w > m || w != w) ? w : m;
+            }
+            if (lane == 0) {
+                const int eg = volume_exp(a.amax, a.wfac, a.fbits);
+                const int ep = min(126, m > 0.f ? min(eg, pow2_exp((double)m * (double)a.wfac, 30)) : eg);
+                s_pass.scale = ldexpf(1.f, ep);
+                s_pass.fold = eg - ep < 63 ? (1LL << (eg - ep)) : 0;   // a larger shift meets only zero sums
+                s_pass.qe = qp + cut;
+            }
+        }
+        __syncthreads();
+        qe = s_pass.qe;   // s_pass is rewritten only after the barrier that ends this pass
         const int nkg = (a.kspan + kShells - 1) / kShells;
         const int units = (qe - qp) * nkg;
         int vq = -1;
@@ -182,7 +279,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
                 const int k = kb + lane, ck = v.cls * a.K + k;
                 int ilo, ihi;
                 if (shell_ring_range(v, __ldg(a.t.Rk + k), __ldg(a.t.ring_cnt + ck), rb2, ilo, ihi)) {
-                    gs = gprime<DT>(a, q, k) * scale;
+                    gs = gprime<DT>(a, q, k) * s_pass.scale;
                     if (gs != 0.f) {
                         n = ihi - ilo + 1;
                         gbase = __ldg(a.t.ring_off + ck) + ilo;
@@ -254,7 +351,8 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
                 const int lz = idx / S2, r = idx - lz * S2, ly = r / S1;
                 const int x = r - ly * S1 + L[0], y = ly + L[1], z = lz + L[2];
                 if (x >= 0 && x < a.nx && y >= 0 && y < a.ny && z >= 0 && z < a.nz) {
-                    const long long vv = (long long)hi * 32768LL + (long long)lo;
+                    // the pass's sum in the volume's unit: exact (eg >= ep)
+                    const long long vv = ((long long)hi * 32768LL + (long long)lo) * s_pass.fold;
                     atomicAdd(a.vacc + ((size_t)z * a.ny + y) * a.nx + x, (unsigned long long)vv);
                 }
             }
@@ -264,14 +362,14 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
 }
 
 __global__ void k_finish_t(const long long *__restrict__ vacc, float *__restrict__ vol, size_t n,
-                           const unsigned int *amax, float gscale, double ds2) {
-    const double unit = ds2 / pow2_scale((double)__uint_as_float(*amax) * (double)gscale, 30);
+                           const unsigned int *amax, float wfac, int fbits, double ds2) {
+    const double unit = ldexp(ds2, -volume_exp(amax, wfac, fbits));
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         vol[i] = (float)((double)vacc[i] * unit);
 }
 
 static int backproject_with(Plan &p, const void *data, float *vol, cudaStream_t s, long long *vacc, unsigned int *amax) {
-    const size_t N = (size_t)p.nx * p.ny * p.nz, M = (size_t)p.Q * p.K;
+    const size_t N = (size_t)p.nx * p.ny * p.nz;
     cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(unsigned int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(vacc, 0, sizeof(long long) * N, s);
     if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_backproject: memset: ") + cudaGetErrorString(e));
@@ -283,17 +381,29 @@ static int backproject_with(Plan &p, const void *data, float *vol, cudaStream_t 
         data = p.d_eir_z;
         dtype = OAT_F32;
     }
-    k_absmax<<<(unsigned)std::min<size_t>((M + 255) / 256, 152 * 8), 256, 0, s>>>(data, M, dtype, amax);
     AdjArgs a;
     a.t = p.t; a.y = data;
     a.vacc = (unsigned long long *)vacc;
+    a.rowmax = p.d_rowmax;
     a.amax = amax;
     a.nx = p.nx; a.ny = p.ny; a.nz = p.nz; a.K = p.K; a.Q = p.Q;
     for (int d = 0; d < 3; ++d) { a.nb[d] = p.adj.nb[d]; a.bs[d] = p.adj.bs[d]; a.O[d] = p.O[d]; a.O_lo[d] = p.O_lo[d]; }
     a.qchunk = p.adj.qchunk; a.kspan = p.adj.kspan; a.qpass = p.adj_qpass;
     a.R0 = p.R0; a.dR = p.dR;
-    a.gscale = p.gscale;
+    a.wfac = p.adj_wfac;
+    a.fbits = p.adj_fbits;
     a.apply_d = p.g.apply_d;
+    {
+        // per-transducer max |g'| (the passes' units) and its maximum (the volume's unit)
+        const unsigned rb = (unsigned)std::min<long long>(((long long)p.Q + 7) / 8, (long long)p.n_sm * 16);
+        float *rm = p.d_rowmax;
+        const int2 *kr = p.d_krange;
+        switch (dtype) {
+            case OAT_F32: k_gprime_rowmax<OAT_F32><<<rb, 256, 0, s>>>(a, kr, rm, amax); break;
+            case OAT_F16: k_gprime_rowmax<OAT_F16><<<rb, 256, 0, s>>>(a, kr, rm, amax); break;
+            default: k_gprime_rowmax<OAT_BF16><<<rb, 256, 0, s>>>(a, kr, rm, amax); break;
+        }
+    }
     const bool prof = p.profiling && p.ev_used[1] + 2 <= (int)p.ev[1].size();
     if (prof) cudaEventRecord(p.ev[1][p.ev_used[1]], s);
     const unsigned grid = (unsigned)p.adj.items;
@@ -315,8 +425,8 @@ static int backproject_with(Plan &p, const void *data, float *vol, cudaStream_t 
     if (prof) { cudaEventRecord(p.ev[1][p.ev_used[1] + 1], s); p.ev_used[1] += 2; }
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_backproject: k_brick_gather_t: ") + cudaGetErrorString(e));
-    k_finish_t<<<(unsigned)std::min<size_t>((N + 255) / 256, 152 * 16), 256, 0, s>>>(
-        (const long long *)vacc, vol, N, amax, p.gscale, p.g.spacing_mm * p.g.spacing_mm);
+    k_finish_t<<<(unsigned)std::min<size_t>((N + 255) / 256, (size_t)p.n_sm * 16), 256, 0, s>>>(
+        (const long long *)vacc, vol, N, amax, p.adj_wfac, p.adj_fbits, p.g.spacing_mm * p.g.spacing_mm);
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_backproject: k_finish_t: ") + cudaGetErrorString(e));
     return OAT_OK;
@@ -330,11 +440,11 @@ int launch_backproject(Plan &p, const void *data, float *vol, cudaStream_t s) {
 // Backprojection without any allocation.  Some callers cannot allocate device memory at the
 // time they need H^T (for example code running inside a pool-managed or graph-building context
 // that forbids cudaMalloc, or a host framework that hands out only the buffers it owns).  For
-// them the scratch of the backprojector -- the 64-bit node accumulator and the max|y| word -- is a
+// them the scratch of the backprojector -- the 64-bit node accumulator and the max|g'| word -- is a
 // file-scope array in device memory, sized for volumes of at most kStaticVoxels voxels.  The
 // array exists on every GPU that loads this library, until the process exits.
 constexpr size_t kStaticVoxels = size_t(1) << 21;          // 2,097,152 voxels (e.g. 128^3)
-constexpr size_t kStaticHeader = 32;                       // 256 bytes: max|y| bit pattern
+constexpr size_t kStaticHeader = 32;                       // 256 bytes: max|g'| bit pattern
 static __device__ __align__(256) unsigned long long g_static_scratch[kStaticHeader + kStaticVoxels];
 
 static std::mutex g_static_mu;

@@ -139,17 +139,13 @@ __device__ __forceinline__ FbpQ fbp_setup(const FbpArgs &a, int q, float cx, flo
 // the integer in the low mantissa bits (fk is already integral, so the sum is exact).
 __device__ __forceinline__ int int_of_integral(float fk) { return __float_as_int(fk + 12582912.f) - 0x4B400000; }
 
-// The (voxel, transducer) terms of two voxels at offsets (dx, dy, dz0|1) from the brick centre,
-// |delta|^2 = dd0|1 (packed DZ, DD): w_q {..} of Eq. disfbp for each, packed.  Per voxel the
-// operations and their rounding are those of the one-voxel form: distance change dD, sample
-// position k~, two-tap interpolation and first difference.  CHECK: samples outside 0 .. K-1
-// count as zero (else every sample read is known to be inside).  STAGED: row is the brick's
-// window of this transducer's samples in shared memory, sample kint - R + j at j (zero outside
-// the record), so that sample k reads row[k - kint + R].
-template <int MODE, typename T>
-__device__ __forceinline__ f32x2 fbp_pair(const FbpQ &Q, const T *row, int K, float dx, float dy, f32x2 DZ, f32x2 DD,
-                                          float sk, int R) {
-    constexpr bool CHECK = MODE == 1, STAGED = MODE == 2;
+// Sample positions of two voxels at offsets (dx, dy, dz0|1) from the brick centre, |delta|^2 =
+// dd0|1 (packed DZ, DD; dx, dy, dz are half-integers, so DD is exact): the distance change
+// DDD = |r_q - r_n| - D (grid units) and KF = k~ - Q.kint, per voxel with the one-voxel form's
+// operations and rounding.  The only place the kernel forms k~ (oat_fbp_sample_positions reads
+// it through this function too).
+__device__ __forceinline__ void fbp_kpos(const FbpQ &Q, float dx, float dy, f32x2 DZ, f32x2 DD, float sk, f32x2 &DDD,
+                                         f32x2 &KF) {
     const float c = fmaf(Q.uy, dy, Q.ux * dx);
     const f32x2 UD = fma2(pk2(Q.uz, Q.uz), DZ, pk2(c, c));
     const float td = 2.f * Q.D;
@@ -161,9 +157,24 @@ __device__ __forceinline__ f32x2 fbp_pair(const FbpQ &Q, const T *row, int K, fl
     const f32x2 DEN = add2(DQ, mul2(S2, pk2(rsqrtf(s2a), rsqrtf(s2b))));
     float dna, dnb;
     upk2(DEN, dna, dnb);
-    const f32x2 DDD = mul2(TT, pk2(__fdividef(1.f, dna), __fdividef(1.f, dnb)));   // distance - D
+    DDD = mul2(TT, pk2(__fdividef(1.f, dna), __fdividef(1.f, dnb)));   // distance - D
+    KF = fma2(DDD, pk2(sk, sk), pk2(Q.kfrac, Q.kfrac));
+}
+
+// The (voxel, transducer) terms of two voxels at offsets (dx, dy, dz0|1) from the brick centre
+// (packed DZ, DD): w_q {..} of Eq. disfbp for each, packed.  Per voxel the
+// operations and their rounding are those of the one-voxel form: distance change dD, sample
+// position k~, two-tap interpolation and first difference.  CHECK: samples outside 0 .. K-1
+// count as zero (else every sample read is known to be inside).  STAGED: row is the brick's
+// window of this transducer's samples in shared memory, sample kint - R + j at j (zero outside
+// the record), so that sample k reads row[k - kint + R].
+template <int MODE, typename T>
+__device__ __forceinline__ f32x2 fbp_pair(const FbpQ &Q, const T *row, int K, float dx, float dy, f32x2 DZ, f32x2 DD,
+                                          float sk, int R) {
+    constexpr bool CHECK = MODE == 1, STAGED = MODE == 2;
+    f32x2 DDD, KF;
+    fbp_kpos(Q, dx, dy, DZ, DD, sk, DDD, KF);
     const f32x2 SK = pk2(sk, sk);
-    const f32x2 KF = fma2(DDD, SK, pk2(Q.kfrac, Q.kfrac));
     float kfa, kfb;
     upk2(KF, kfa, kfb);
     const float fka = floorf(kfa), fkb = floorf(kfb);
@@ -264,16 +275,53 @@ __global__ void __launch_bounds__(kFbpThreads) k_fbp(FbpArgs a) {
     }
 }
 
-int launch_fbp(Plan &p, const void *data, float *vol, cudaStream_t s) {
-    FbpArgs a;
-    a.xd = p.d_fbp; a.p = data; a.vol = vol;
+// k~ of (node, transducer) pairs exactly as k_fbp forms it: the node's brick centre and offset,
+// fbp_setup for the transducer, then fbp_kpos (the node in the first of the two packed lanes).
+// out[i] = kint + KF in double (exact); NaN for a transducer index outside 0 .. Q-1.
+__global__ void k_fbp_kpos(FbpArgs a, const int *__restrict__ nodes, const int *__restrict__ qs, int n, double *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int ix = nodes[3 * i], iy = nodes[3 * i + 1], iz = nodes[3 * i + 2], q = qs[i];
+    if (q < 0 || q >= a.Q) { out[i] = __longlong_as_double(0x7ff8000000000000LL); return; }
+    const int bx = ix >= 0 ? ix / kFbpB : -((-ix + kFbpB - 1) / kFbpB);
+    const int by = iy >= 0 ? iy / kFbpB : -((-iy + kFbpB - 1) / kFbpB);
+    const int bz = iz >= 0 ? iz / kFbpB : -((-iz + kFbpB - 1) / kFbpB);
+    const FbpQ Q = fbp_setup(a, q, bx * kFbpB + 3.5f, by * kFbpB + 3.5f, bz * kFbpB + 3.5f);
+    const float dx = (ix - bx * kFbpB) - 3.5f, dy = (iy - by * kFbpB) - 3.5f, dz = (iz - bz * kFbpB) - 3.5f;
+    const float dxy = dx * dx + dy * dy, dd = dxy + dz * dz;
+    f32x2 DDD, KF;
+    fbp_kpos(Q, dx, dy, pk2(dz, dz), pk2(dd, dd), a.sk_hi, DDD, KF);
+    float kf, kf2;
+    upk2(KF, kf, kf2);
+    out[i] = (double)Q.kint + (double)kf;
+}
+
+static void fbp_args(const Plan &p, FbpArgs &a) {
+    a.xd = p.d_fbp;
     a.nx = p.nx; a.ny = p.ny; a.nz = p.nz; a.K = p.K; a.Q = p.Q;
     a.bx = (p.nx + kFbpB - 1) / kFbpB; a.by = (p.ny + kFbpB - 1) / kFbpB;
-    const int bz = (p.nz + kFbpB - 1) / kFbpB;
     const double sk = p.g.spacing_mm / (p.g.c_mm_per_us * p.dt), t0 = p.g.t_min_us / p.dt;
     a.sk_hi = (float)sk; a.sk_lo = (float)(sk - (double)a.sk_hi);
     a.t0_hi = (float)t0; a.t0_lo = (float)(t0 - (double)a.t0_hi);
     a.scale = -1.0 / (M_PI * p.g.gruneisen * p.g.c_mm_per_us * p.dt);
+}
+
+int launch_fbp_kpos(Plan &p, const int *nodes, const int *qs, int n, double *out, cudaStream_t s) {
+    if (n == 0) return OAT_OK;
+    FbpArgs a;
+    fbp_args(p, a);
+    a.p = nullptr; a.vol = nullptr; a.R = 0; a.W = 0;
+    k_fbp_kpos<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, nodes, qs, n, out);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? OAT_OK : set_error(OAT_ERR_CUDA, std::string("oat_fbp_sample_positions: ") + cudaGetErrorString(e));
+}
+
+int launch_fbp(Plan &p, const void *data, float *vol, cudaStream_t s) {
+    FbpArgs a;
+    fbp_args(p, a);
+    a.p = data; a.vol = vol;
+    const int bz = (p.nz + kFbpB - 1) / kFbpB;
+    const double sk = p.g.spacing_mm / (p.g.c_mm_per_us * p.dt);
     const unsigned blocks = (unsigned)((size_t)a.bx * a.by * bz);
     // every voxel of a brick lies within 3.5 sqrt(3) grid units of its centre, so its sample
     // index is within that times sk of the centre's (the kernel's reach, plus a margin): the

@@ -5,7 +5,7 @@
 //                  ends (or u = g without D) in double precision -- the difference of
 //                  neighbouring samples cancels by one to three digits -- with one rounding to
 //                  float32 / float16 / bfloat16 at the end.
-// k_absmax         max |x| of a buffer (the fixed-point units of both directions).
+// k_absmax         max |x| of a buffer (the projector's fixed-point unit).
 // k_brick_gather<COUNT>  lattice points whose stencil touches the grid (oat_plan_query).
 // k_brick_gather<AREA>   the same gather with each point's value scaled by its ring's
 //                  exact-strip-area weight factor (OAT_LATTICE_EXACT_AREA).
@@ -252,7 +252,7 @@ int launch_project(Plan &p, const float *vol, void *data, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(p.d_amax, 0, sizeof(unsigned int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p.d_gacc, 0, sizeof(long long) * (size_t)p.Q * p.K, s);
     if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_project: memset: ") + cudaGetErrorString(e));
-    k_absmax<<<(unsigned)std::min<size_t>((N + 255) / 256, 152 * 8), 256, 0, s>>>(vol, N, OAT_F32, p.d_amax);
+    k_absmax<<<(unsigned)std::min<size_t>((N + 255) / 256, (size_t)p.n_sm * 8), 256, 0, s>>>(vol, N, OAT_F32, p.d_amax);
     FwdArgs a;
     fill_forward_args(p, vol, a);
     const bool prof = p.profiling && p.ev_used[0] + 2 <= (int)p.ev[0].size();
@@ -264,7 +264,7 @@ int launch_project(Plan &p, const float *vol, void *data, cudaStream_t s) {
     if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_project: k_brick_gather: ") + cudaGetErrorString(e));
     if (p.eir_n > 0) return launch_apply_d_eir(p, data, s);
     const size_t n = (size_t)p.Q * p.K;
-    const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
+    const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)p.n_sm * 16);
     const int dt = p.g.data_dtype;
     const double bp = p.fwd_bound, ds2 = p.g.spacing_mm * p.g.spacing_mm;
     const long long *g = (const long long *)p.d_gacc;

@@ -90,8 +90,10 @@ struct Plan {
     long long max_shell_points = 0;   // largest N_i-ring lattice of one shell (fixed-point bound)
     bool area = false;                // exact strip-area point weights (ring_w)
     double fwd_bound = 0.0;           // max over shells of the sum of point weights / Delta_s^2
-    float gscale = 1.f;               // max |g'| / max |y|: 2 max_k C_D/tau_k with D, 1 without
+    float adj_wfac = 1.f;             // bound of a point's weight factor in G^T (exact areas; else 1)
+    int adj_fbits = 30;               // G^T volume accumulator: a contribution is <= 2^adj_fbits units
     int adj_qpass = 1;                // transducers per backprojector pass (bounds the 32-bit halves)
+    int n_sm = 0;                     // streaming multiprocessors of the plan's device (grid sizes)
     BrickCfg fwd, adj;                 // brick tilings of the projector and the backprojector
     long long table_bytes = 0, scratch_bytes = 0;
     std::vector<long long> cls_points;   // [n_cls * K] points per (class, k)
@@ -101,7 +103,9 @@ struct Plan {
     DevTables t{};
     long long *d_gacc = nullptr;     // [Q][K] scratch: fixed-point sums of G alpha
     long long *d_vacc = nullptr;     // [nz][ny][nx] scratch: fixed-point node sums of G^T g'
-    unsigned int *d_amax = nullptr;  // [2] scratch: max|alpha| and max|y| bit patterns
+    unsigned int *d_amax = nullptr;  // [2] scratch: max|alpha| and max|g'| bit patterns
+    float *d_rowmax = nullptr;       // [Q] scratch: per-transducer max |g'| of the backprojector
+    const int2 *d_krange = nullptr;  // [Q] (in the tables) samples whose shells can reach the grid
     unsigned long long *d_count = nullptr;  // point counter of oat_plan_query
 
     // profiling
@@ -126,6 +130,8 @@ struct Plan {
 
 // status helpers (abi.cpp)
 int set_error(int code, const std::string &msg);
+// SM count of the current device (looked up once per device; 1 if the query fails)
+int current_sm_count();
 
 // kernels' host launchers (forward.cu, adjoint.cu)
 int launch_project(Plan &p, const float *vol, void *data, cudaStream_t s);
@@ -139,6 +145,7 @@ int set_eir_attributes(const Plan &p);
 int launch_apply_d_eir(Plan &p, void *data, cudaStream_t s);
 int launch_eir_t(Plan &p, const void *y, float *z, cudaStream_t s);
 int launch_fbp(Plan &p, const void *data, float *vol, cudaStream_t s);
+int launch_fbp_kpos(Plan &p, const int *nodes, const int *qs, int n, double *out, cudaStream_t s);
 int set_adjoint_attributes();
 int set_forward_attributes();
 size_t forward_smem_bytes();

@@ -226,6 +226,16 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
     p->area = area;
     p->fwd_bound = area ? wsum_max * (1.0 + 1e-6) : (double)p->max_shell_points;
 
+    {
+        // grid sizes follow the device's SM count (the first device call: host validation is done)
+        cudaError_t ea = cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, device);
+        if (ea != cudaSuccess || p->n_sm < 1) {
+            delete p;
+            cudaGetLastError();
+            return set_error(OAT_ERR_CUDA, std::string("oat_plan_create: cudaDeviceGetAttribute(SM count): ") +
+                                               cudaGetErrorString(ea));
+        }
+    }
     // brick tilings of the cells [-1, n-1] for the two directions
     auto tile = [&](BrickCfg &bc, int B, size_t node_bytes) {
         const int n[3] = {p->nx, p->ny, p->nz};
@@ -240,7 +250,7 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
         }
         const double rb = 0.5 * std::sqrt(diag2) + 0.05;
         bc.kspan = (int)std::ceil(2.0 * rb / (g.c_mm_per_us * p->dt / ds)) + 2;
-        const long long target = 152LL * 8;
+        const long long target = (long long)p->n_sm * 8;
         long long chunks = std::max(1LL, std::min<long long>(Q, (target + bricks - 1) / bricks));
         bc.qchunk = (int)((Q + chunks - 1) / chunks);
         bc.items = bricks * ((Q + bc.qchunk - 1) / bc.qchunk);
@@ -262,6 +272,11 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
             return set_error(OAT_ERR_UNSUPPORTED, "oat_plan_create: shells too dense for the backprojector's "
                                                   "fixed-point accumulation (c dt / spacing too small)");
         }
+        // the volume accumulator's unit: a node receives at most per_q Q contributions of at
+        // most 2^adj_fbits units each, which must stay below 2^62 in magnitude
+        int lb = 0;
+        while ((1LL << lb) < per_q * (long long)Q) ++lb;
+        p->adj_fbits = 62 - lb;
     }
 
     std::vector<float> Rk(K), wD(K);
@@ -273,10 +288,32 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
         wD[k] = tau > 0.0 ? (float)(p->cd / tau) : 0.f;
         wD64[k] = tau > 0.0 ? p->cd / tau : 0.0;
     }
-    double wmax = 0.0;
-    for (int k = 0; k < K; ++k) wmax = std::max(wmax, (double)wD[k]);
-    p->gscale = g.apply_d ? (float)(2.0 * wmax * (1.0 + 1e-6)) : 1.f;
-    if (area) p->gscale = (float)((double)p->gscale * wring_max * (1.0 + 1e-6));
+    // G^T: a point's weight factor is at most wring_max with exact strip areas (1 otherwise)
+    p->adj_wfac = area ? (float)(wring_max * (1.0 + 1e-6)) : 1.f;
+
+    // per transducer, the samples whose shells can hold a point in a cell of the grid (the node
+    // box grown by one spacing, the trilinear support), with two samples of margin: the
+    // backprojector bounds g' over these only
+    std::vector<int2> krange(Q);
+    {
+        const double lo[3] = {g.origin_mm[0] - ds, g.origin_mm[1] - ds, g.origin_mm[2] - ds};
+        const double hi[3] = {g.origin_mm[0] + ds * g.nx, g.origin_mm[1] + ds * g.ny, g.origin_mm[2] + ds * g.nz};
+        for (int q = 0; q < Q; ++q) {
+            double dn = 0.0, df = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                const double x = p->pos[3 * q + d];
+                const double near = x < lo[d] ? lo[d] - x : (x > hi[d] ? x - hi[d] : 0.0);
+                const double far = std::max(std::fabs(x - lo[d]), std::fabs(x - hi[d]));
+                dn += near * near;
+                df += far * far;
+            }
+            const double k0 = std::floor((std::sqrt(dn) / g.c_mm_per_us - g.t_min_us) / p->dt) - 2.0;
+            const double k1 = std::ceil((std::sqrt(df) / g.c_mm_per_us - g.t_min_us) / p->dt) + 2.0;
+            const int a = (int)std::max(0.0, std::min((double)K, k0));
+            const int b = (int)std::max(-1.0, std::min((double)K - 1, k1));
+            krange[q] = make_int2(a, b);   // empty when a > b
+        }
+    }
 
     // one device blob for every table
     std::vector<unsigned char> blob;
@@ -284,6 +321,7 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
     size_t o_xd = push_bytes(blob, xd), o_an = push_bytes(blob, anchors);
     size_t o_rk = push_bytes(blob, Rk), o_wd = push_bytes(blob, wD), o_wd64 = push_bytes(blob, wD64);
     size_t o_rw = push_bytes(blob, ring_w);
+    size_t o_kr = push_bytes(blob, krange);
     std::vector<float4>().swap(anchors);
     p->table_bytes = (long long)blob.size();
 
@@ -300,6 +338,7 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
         if (p->d_gacc) cudaFree(p->d_gacc);
         if (p->d_vacc) cudaFree(p->d_vacc);
         if (p->d_amax) cudaFree(p->d_amax);
+        if (p->d_rowmax) cudaFree(p->d_rowmax);
         if (p->d_fbp) cudaFree(p->d_fbp);
         delete p;
         cudaGetLastError();
@@ -314,6 +353,7 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
     if ((e = cudaMalloc(&p->d_gacc, g_bytes)) != cudaSuccess) return fail(e, "cudaMalloc(G scratch)");
     if ((e = cudaMalloc(&p->d_vacc, v_bytes)) != cudaSuccess) return fail(e, "cudaMalloc(G^T scratch)");
     if ((e = cudaMalloc(&p->d_amax, 256)) != cudaSuccess) return fail(e, "cudaMalloc(scale scratch)");
+    if ((e = cudaMalloc(&p->d_rowmax, sizeof(float) * (size_t)Q)) != cudaSuccess) return fail(e, "cudaMalloc(row maxima)");
     // FBP table: transducer positions in index units as float pairs; weights set later
     p->fbp_host.resize(2 * (size_t)Q);
     for (int q = 0; q < Q; ++q) {
@@ -327,7 +367,7 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
         cudaSuccess)
         return fail(e, "cudaMemcpy(FBP table)");
     p->d_count = (unsigned long long *)((char *)p->d_amax + 128);
-    p->scratch_bytes = (long long)(g_bytes + v_bytes + 256 + sizeof(float4) * p->fbp_host.size());
+    p->scratch_bytes = (long long)(g_bytes + v_bytes + 256 + sizeof(float) * (size_t)Q + sizeof(float4) * p->fbp_host.size());
     if (set_forward_attributes() != OAT_OK || set_adjoint_attributes() != OAT_OK) {
         std::string msg = std::string("oat_plan_create: ") + oat_last_error();
         fail(cudaSuccess, "kernel attributes");
@@ -345,6 +385,7 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
     p->t.wD = (const float *)(base + o_wd);
     p->t.wD64 = (const double *)(base + o_wd64);
     p->t.ring_w = area ? (const float *)(base + o_rw) : nullptr;
+    p->d_krange = (const int2 *)(base + o_kr);
     *out = p;
     return OAT_OK;
 }
@@ -361,6 +402,7 @@ void plan_destroy(Plan *p) {
     if (p->d_gacc) cudaFree(p->d_gacc);
     if (p->d_vacc) cudaFree(p->d_vacc);
     if (p->d_amax) cudaFree(p->d_amax);
+    if (p->d_rowmax) cudaFree(p->d_rowmax);
     if (p->d_eir) cudaFree(p->d_eir);
     if (p->d_eir_z) cudaFree(p->d_eir_z);
     cudaSetDevice(prev);

@@ -39,7 +39,7 @@ using namespace oat;
 extern "C" int oat_probe_read(const void *d_buf, long long n_bytes, int reps, float *d_sink, void *stream) {
     if (!d_buf || !d_sink || n_bytes <= 0 || (n_bytes & 15) || ((uintptr_t)d_buf & 15) || reps < 1)
         return set_error(OAT_ERR_INVALID_ARG, "oat_probe_read: bad size or pointer");
-    k_probe_read<<<152 * 4, 512, 0, (cudaStream_t)stream>>>((const float4 *)d_buf, n_bytes / 16, reps, d_sink);
+    k_probe_read<<<(unsigned)(4 * current_sm_count()), 512, 0, (cudaStream_t)stream>>>((const float4 *)d_buf, n_bytes / 16, reps, d_sink);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? OAT_OK : set_error(OAT_ERR_CUDA, std::string("oat_probe_read: ") + cudaGetErrorString(e));
 }

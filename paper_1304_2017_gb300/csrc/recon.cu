@@ -126,7 +126,9 @@ __global__ void __launch_bounds__(kRThreads) k_tv_value(Vol v, const float *__re
     block_add(s, acc);
 }
 
-static unsigned grid_for(long long n) { return (unsigned)std::min<long long>((n + kRThreads - 1) / kRThreads, 152LL * 8); }
+static unsigned grid_for(long long n) {
+    return (unsigned)std::max<long long>(1, std::min<long long>((n + kRThreads - 1) / kRThreads, 8LL * current_sm_count()));
+}
 
 static bool al16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 

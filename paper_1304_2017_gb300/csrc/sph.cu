@@ -465,7 +465,7 @@ int oat_sph_create(const oat_geometry *geom, int n_freq, double f0_mhz, double d
     // forward slabs: enough (warp task, slab) work items for about 16 waves of resident blocks,
     // slabs of at least 8192 voxels, slab totals within 1 GiB
     {
-        int sms = 152, per_sm = 1;
+        int sms = 1, per_sm = 1;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sph_fwd, kSphFwdThreads, 0);
         const long long tasks = (long long)Q * p->nseg;
@@ -515,7 +515,7 @@ int oat_sph_project(oat_sph op, const float *d_alpha, float *d_u, void *stream) 
     const dim3 grid((unsigned)((warps + kSphFwdThreads / 32 - 1) / (kSphFwdThreads / 32)), (unsigned)p->n_slab);
     k_sph_fwd<<<grid, kSphFwdThreads, 0, s>>>(a);
     const long long M = (long long)p->Q * p->L;
-    k_sph_reduce<<<(unsigned)std::min<long long>((M + 255) / 256, 152 * 8), 256, 0, s>>>(
+    k_sph_reduce<<<(unsigned)std::min<long long>((M + 255) / 256, 8LL * current_sm_count()), 256, 0, s>>>(
         p->d_part, p->d_p0, reinterpret_cast<float2 *>(d_u), M, p->L, p->n_slab);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? OAT_OK : set_error(OAT_ERR_CUDA, std::string("oat_sph_project: ") + cudaGetErrorString(e));
@@ -531,7 +531,7 @@ int oat_sph_backproject(oat_sph op, const float *d_u, float *d_alpha, void *stre
         return set_error(OAT_ERR_CUDA, std::string("oat_sph_backproject: ") + cudaGetErrorString(dg.err));
     const cudaStream_t s = (cudaStream_t)stream;
     const long long M = (long long)p->Q * p->L;
-    k_sph_conj<<<(unsigned)std::min<long long>((M + 255) / 256, 152 * 8), 256, 0, s>>>(
+    k_sph_conj<<<(unsigned)std::min<long long>((M + 255) / 256, 8LL * current_sm_count()), 256, 0, s>>>(
         reinterpret_cast<const float2 *>(d_u), p->d_p0, p->d_v, M, p->L);
     SphArgs a = sph_args(*p);
     a.v = p->d_v;

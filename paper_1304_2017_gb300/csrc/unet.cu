@@ -288,7 +288,9 @@ __global__ void k_adam(long long n, float *p, const float *__restrict__ g, float
     }
 }
 
-static unsigned grid1(long long n) { return (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 16)); }
+static unsigned grid1(long long n) {
+    return (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 16LL * current_sm_count()));
+}
 
 static int launched(const char *what) {
     cudaError_t e = cudaGetLastError();

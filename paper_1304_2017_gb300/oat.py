@@ -71,13 +71,14 @@ def _load():
     lib.oat_dot.argtypes = [ll, vp, vp, vp, vp]
     lib.oat_tv_value.argtypes = [i32, i32, i32, vp, vp, vp]
     lib.oat_probe_read.argtypes = [vp, ll, i32, vp, vp]
+    lib.oat_fbp_sample_positions.argtypes = [vp, vp, vp, i32, vp, vp]
     lib.oat_sph_create.argtypes = [ctypes.POINTER(oat_geometry), i32, ctypes.c_double, ctypes.c_double,
                                    ctypes.POINTER(ctypes.c_double), i32, ctypes.POINTER(vp)]
     lib.oat_sph_project.argtypes = [vp, vp, vp, vp]
     lib.oat_sph_backproject.argtypes = [vp, vp, vp, vp]
     lib.oat_sph_destroy.argtypes = [vp]
     for name in ("oat_fista_residual", "oat_tv_prox", "oat_fista_momentum", "oat_dot", "oat_tv_value",
-                 "oat_probe_read", "oat_sph_create", "oat_sph_project", "oat_sph_backproject", "oat_sph_destroy"):
+                 "oat_probe_read", "oat_fbp_sample_positions", "oat_sph_create", "oat_sph_project", "oat_sph_backproject", "oat_sph_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     lib.oat_last_error.restype = ctypes.c_char_p
     lib.oat_version.restype = ctypes.c_int
@@ -198,6 +199,10 @@ def oat_tv_value(nx, ny, nz, x, acc, stream=0):
     return _check(lib.oat_tv_value(nx, ny, nz, _p(x), _p(acc), _p(stream)))
 
 
+def oat_fbp_sample_positions(handle, d_nodes, d_transducers, n, d_out, stream=0):
+    return _check(lib.oat_fbp_sample_positions(handle, _p(d_nodes), _p(d_transducers), int(n), _p(d_out), _p(stream)))
+
+
 def oat_probe_read(buf, n_bytes, reps, sink, stream=0):
     return _check(lib.oat_probe_read(_p(buf), n_bytes, reps, _p(sink), _p(stream)))
 
@@ -311,6 +316,18 @@ class Plan:
         self._checked(out, self.vol_shape, torch.float32, "out")
         oat_fbp(self.handle, data.data_ptr(), out.data_ptr(), self._stream())
         return out
+
+    def fbp_sample_positions(self, nodes, transducers):
+        """k~ of (node, transducer) pairs as oat_fbp computes it: nodes int (n, 3) (ix, iy, iz),
+        transducers int (n,); returns a float64 numpy array (n,)."""
+        torch = self._torch
+        nd = torch.as_tensor(np.ascontiguousarray(nodes, dtype=np.int32).reshape(-1, 3), device=self.device)
+        qs = torch.as_tensor(np.ascontiguousarray(transducers, dtype=np.int32).reshape(-1), device=self.device)
+        if nd.shape[0] != qs.shape[0]:
+            raise ValueError("nodes and transducers differ in length")
+        out = torch.empty(qs.shape[0], dtype=torch.float64, device=self.device)
+        oat_fbp_sample_positions(self.handle, nd.data_ptr(), qs.data_ptr(), qs.shape[0], out.data_ptr(), self._stream())
+        return out.cpu().numpy()
 
     def backproject(self, data, out=None):
         torch = self._torch

@@ -96,3 +96,21 @@ def test_integer_crossing_allowance_covers_a_shift():
     beyond = np.maximum(np.abs(b - a) - amb, 0.0)
     assert amb[0, 0, 0] > 0 and abs(b - a)[0, 0, 0] > 1e-4 * np.abs(a).max()   # a real crossing
     assert np.linalg.norm(beyond) <= 1e-6 * np.linalg.norm(a)
+
+
+def test_sample_positions_at_known_distances():
+    """sample_positions (Eq. linearint's k~) at nodes whose distance to the transducer is known:
+    a transducer on the z axis and nodes on that axis, with t_min chosen so that node 0 sits
+    exactly on sample 37 and each further node (one spacing closer) 0.27 / (c dt) samples earlier."""
+    g = W.make_geometry(9, 0.27, 1, 1, 6.0, 200, positions_mm=[[0.0, 0.0, 6.0]])
+    dt = 1.0 / g.fs_mhz
+    xs, ys, zs = g.node_coords_mm()
+    ix = int(np.argmin(np.abs(xs)))
+    iy = int(np.argmin(np.abs(ys)))
+    assert xs[ix] == 0.0 and ys[iy] == 0.0                 # odd node count: a node column on the axis
+    d0 = 6.0 - zs[0]
+    g.t_min_us = d0 / g.c_mm_per_us - 37 * dt
+    nodes = np.array([[ix, iy, iz] for iz in range(g.nz)])
+    kt = F.sample_positions(g, nodes, np.zeros(g.nz, int))
+    want = 37.0 - np.arange(g.nz) * 0.27 / (g.c_mm_per_us * dt)
+    assert np.allclose(kt, want, rtol=0, atol=1e-10), np.abs(kt - want).max()

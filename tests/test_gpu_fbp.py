@@ -8,12 +8,14 @@ are read exactly, so the reference gets the same rounded values.
 
 Eq. disfbp is discontinuous in the sample position: where k~ crosses an integer the one-sided
 difference p_{k+1} - p_k moves to the next pair, so a rounding difference that moves k~ across
-an integer changes that term by the second difference of the data.  Where k~ lies within 1e-4
-of a sample (about 1e-4 of the pairs) both sides are valid readings; the comparison allows each
-node the reference's total change over such pairs (`ambiguity`) and holds everything else to
-the tolerance.  The data are band-limited, as measured pressure is (Gaussian pulses several
-samples wide, or the forward model's data of a smooth object): for white noise the second
-difference is as large as the data."""
+an integer changes that term by the second difference of the data.  The kernel's k~ error is
+measured directly (oat_fbp_sample_positions against the FP64 definition, `KT_MAX`); where the
+exact k~ lies within EPS_K = 2 KT_MAX of a sample both sides are readings the FP32 kernel may
+take, so the comparison allows each node the reference's total change over such pairs
+(`ambiguity`) and holds everything else to the tolerance.  The raw error is printed beside it.
+The data are band-limited, as measured pressure is (Gaussian pulses several samples wide, or the
+forward model's data of an object): for white noise the second difference is as large as the
+data."""
 import numpy as np
 import pytest
 
@@ -46,7 +48,11 @@ def rel_beyond(got, want, amb):
     return float(np.linalg.norm(d) / np.linalg.norm(want))
 
 
-EPS_K = 1e-4
+# the largest k~ error of the kernel (samples), measured by test_fbp_sample_position_accuracy on
+# every small case and on sampled pairs of the 256^3 / 23,040-transducer scan, and the window of
+# the integer-crossing allowance: twice that
+KT_MAX = 1e-5
+EPS_K = 2 * KT_MAX
 
 
 def smooth_data(geom, seed, width=6.0, n_pulses=3):
@@ -78,8 +84,12 @@ def blob_phantom(geom, seed, n=3, sigma_vox=2.5):
 def _data(geom, kind, seed):
     if kind == "smooth":
         return smooth_data(geom, seed)
-    # the forward model's own data (the oracle, FP64) of a smooth object
     import oracle
+    if kind == "spheres":
+        # the forward model's own data (the oracle, FP64) of uniform spheres: sharp edges, so large
+        # second differences where the pulses switch on and off
+        return oracle.H(geom, W.spheres_phantom(geom, 3, seed=seed)).astype(np.float32)
+    # the forward model's own data (the oracle, FP64) of a smooth object
     return oracle.H(geom, blob_phantom(geom, seed)).astype(np.float32)
 
 
@@ -91,6 +101,7 @@ CASES = {
     "tmin0": (lambda: W.make_geometry(12, 0.29, 2, 4, 6.07, 120, t_min_us=0.0), "smooth"),
     "window_cut": (lambda: W.make_geometry(14, 0.31, 3, 4, 8.11, 30), "smooth"),
     "physical": (lambda: W.make_geometry(20, 0.251, 6, 8, 8.03, 160), "forward"),
+    "physical_spheres": (lambda: W.make_geometry(20, 0.251, 6, 8, 8.03, 160), "spheres"),
     # coarse grid at 40 MHz: about 16 samples per grid spacing, so a brick's sample windows are
     # too wide to stage in shared memory and the kernel reads the data directly
     "coarse_direct": (lambda: W.make_geometry(10, 0.61, 3, 4, 9.13, 400, fs_mhz=40.0), "smooth"),
@@ -103,7 +114,7 @@ def test_fbp_matches_reference(env, case, dtype):
     torch, oat = env
     make, kind = CASES[case]
     geom = make()
-    n_r = {"ragged": 3, "tmin0": 2, "window_cut": 3, "physical": 6, "coarse_direct": 3}[case]
+    n_r = {"ragged": 3, "tmin0": 2, "window_cut": 3, "physical": 6, "physical_spheres": 6, "coarse_direct": 3}[case]
     n_v = geom.n_transducers // n_r
     w = F.arc_weights(geom.positions_mm, n_r, n_v)
     p = _data(geom, kind, 11)
@@ -113,9 +124,44 @@ def test_fbp_matches_reference(env, case, dtype):
     got = plan.fbp(pt).cpu().numpy()
     want, amb = F.fbp(geom, pt.float().cpu().numpy(), w, ambiguity=EPS_K)
     assert np.abs(want).max() > 0
-    print(case, dtype, "rel", rel(got, want), "beyond the allowance", rel_beyond(got, want, amb))
+    print(f"fbp {case} dtype {dtype}: raw rel-L2 {rel(got, want):.3e}, beyond the allowance "
+          f"{rel_beyond(got, want, amb):.3e}")
     assert rel_beyond(got, want, amb) <= TOL, (rel(got, want), rel_beyond(got, want, amb))
     plan.close()
+
+
+def _kt_errors(oat, geom, nodes, qs):
+    plan = oat.Plan(geom)
+    got = plan.fbp_sample_positions(nodes, qs)
+    plan.close()
+    want = F.sample_positions(geom, nodes, qs)
+    return np.abs(got - want)
+
+
+@pytest.mark.parametrize("case", sorted(CASES) + ["c2_sampled"])
+def test_fbp_sample_position_accuracy(env, case):
+    """The kernel's own k~ (oat_fbp_sample_positions runs the arithmetic of k_fbp) against the
+    FP64 definition: every (node, transducer) pair of the small cases, 400,000 sampled pairs of
+    the 256^3 / 23,040-transducer scan (distances up to about 450 grid units).  The largest error
+    bounds the integer-crossing window EPS_K used by the parity tests."""
+    torch, oat = env
+    if case == "c2_sampled":
+        geom = W.config("c2")
+        rng = np.random.default_rng(17)
+        n = 400_000
+        nodes = rng.integers(0, 256, size=(n, 3))
+        qs = rng.integers(0, geom.n_transducers, size=n)
+    else:
+        geom = CASES[case][0]()
+        iz, iy, ix = np.meshgrid(np.arange(geom.nz), np.arange(geom.ny), np.arange(geom.nx), indexing="ij")
+        grid = np.stack([ix.ravel(), iy.ravel(), iz.ravel()], axis=1)
+        nodes = np.repeat(grid, geom.n_transducers, axis=0)
+        qs = np.tile(np.arange(geom.n_transducers), len(grid))
+    err = _kt_errors(oat, geom, nodes, qs)
+    print(f"fbp k~ error {case}: max {err.max():.3e} samples, rms {np.sqrt((err ** 2).mean()):.3e} "
+          f"over {len(err)} pairs")
+    assert np.isfinite(err).all()
+    assert err.max() <= KT_MAX, err.max()
 
 
 def test_fbp_full_size_sampled_nodes(env):
@@ -133,7 +179,7 @@ def test_fbp_full_size_sampled_nodes(env):
     nodes[:8, 0] = 0; nodes[8:16, 1] = 255; nodes[16:24, 2] = 0
     want, amb = F.fbp(geom, p, w, nodes=nodes, ambiguity=EPS_K)
     got_s = got[nodes[:, 2], nodes[:, 1], nodes[:, 0]]
-    print("fbp full size:", rel(got_s, want), rel_beyond(got_s, want, amb))
+    print(f"fbp full size: raw rel-L2 {rel(got_s, want):.3e}, beyond the allowance {rel_beyond(got_s, want, amb):.3e}")
     assert rel_beyond(got_s, want, amb) <= TOL, (rel(got_s, want), rel_beyond(got_s, want, amb))
     plan.close()
 
