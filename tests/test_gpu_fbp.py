@@ -9,8 +9,8 @@ are read exactly, so the reference gets the same rounded values.
 Eq. disfbp is discontinuous in the sample position: where k~ crosses an integer the one-sided
 difference p_{k+1} - p_k moves to the next pair, so a rounding difference that moves k~ across
 an integer changes that term by the second difference of the data.  The kernel's k~ error is
-measured directly (oat_fbp_sample_positions against the FP64 definition, `KT_MAX`); where the
-exact k~ lies within EPS_K = 2 KT_MAX of a sample both sides are readings the FP32 kernel may
+measured directly (oat_fbp_sample_positions against the FP64 definition, `kt_max`); where the
+exact k~ lies within twice that error bound of a sample both sides are readings the FP32 kernel may
 take, so the comparison allows each node the reference's total change over such pairs
 (`ambiguity`) and holds everything else to the tolerance.  The raw error is printed beside it.
 The data are band-limited, as measured pressure is (Gaussian pulses several samples wide, or the
@@ -48,11 +48,20 @@ def rel_beyond(got, want, amb):
     return float(np.linalg.norm(d) / np.linalg.norm(want))
 
 
-# the largest k~ error of the kernel (samples), measured by test_fbp_sample_position_accuracy on
-# every small case and on sampled pairs of the 256^3 / 23,040-transducer scan, and the window of
-# the integer-crossing allowance: twice that
-KT_MAX = 1e-5
-EPS_K = 2 * KT_MAX
+# The kernel's k~ error is a distance error: at most KT_GRID grid units (measured by
+# test_fbp_sample_position_accuracy on every small case and on sampled pairs of the 256^3 /
+# 23,040-transducer scan), i.e. KT_GRID ds / (c dt) samples.  The window of the integer-crossing
+# allowance is twice that bound.
+KT_GRID = 1.5e-6
+
+
+def kt_max(geom):
+    """Bound of the kernel's k~ error in samples for this geometry."""
+    return KT_GRID * geom.spacing_mm * geom.fs_mhz / geom.c_mm_per_us
+
+
+def eps_k(geom):
+    return 2.0 * kt_max(geom)
 
 
 def smooth_data(geom, seed, width=6.0, n_pulses=3):
@@ -122,7 +131,7 @@ def test_fbp_matches_reference(env, case, dtype):
     plan.set_fbp_weights(w)
     pt = torch.from_numpy(p).cuda().to(plan.torch_data_dtype)
     got = plan.fbp(pt).cpu().numpy()
-    want, amb = F.fbp(geom, pt.float().cpu().numpy(), w, ambiguity=EPS_K)
+    want, amb = F.fbp(geom, pt.float().cpu().numpy(), w, ambiguity=eps_k(geom))
     assert np.abs(want).max() > 0
     print(f"fbp {case} dtype {dtype}: raw rel-L2 {rel(got, want):.3e}, beyond the allowance "
           f"{rel_beyond(got, want, amb):.3e}")
@@ -143,7 +152,7 @@ def test_fbp_sample_position_accuracy(env, case):
     """The kernel's own k~ (oat_fbp_sample_positions runs the arithmetic of k_fbp) against the
     FP64 definition: every (node, transducer) pair of the small cases, 400,000 sampled pairs of
     the 256^3 / 23,040-transducer scan (distances up to about 450 grid units).  The largest error
-    bounds the integer-crossing window EPS_K used by the parity tests."""
+    bounds the integer-crossing window used by the parity tests (twice the bound)."""
     torch, oat = env
     if case == "c2_sampled":
         geom = W.config("c2")
@@ -158,10 +167,11 @@ def test_fbp_sample_position_accuracy(env, case):
         nodes = np.repeat(grid, geom.n_transducers, axis=0)
         qs = np.tile(np.arange(geom.n_transducers), len(grid))
     err = _kt_errors(oat, geom, nodes, qs)
-    print(f"fbp k~ error {case}: max {err.max():.3e} samples, rms {np.sqrt((err ** 2).mean()):.3e} "
-          f"over {len(err)} pairs")
+    sk = geom.spacing_mm * geom.fs_mhz / geom.c_mm_per_us
+    print(f"fbp k~ error {case}: max {err.max():.3e} samples ({err.max() / sk:.3e} grid units), "
+          f"rms {np.sqrt((err ** 2).mean()):.3e} samples over {len(err)} pairs; bound {kt_max(geom):.3e}")
     assert np.isfinite(err).all()
-    assert err.max() <= KT_MAX, err.max()
+    assert err.max() <= kt_max(geom), (err.max(), kt_max(geom))
 
 
 def test_fbp_full_size_sampled_nodes(env):
@@ -177,7 +187,7 @@ def test_fbp_full_size_sampled_nodes(env):
     rng = np.random.default_rng(5)
     nodes = rng.integers(0, 256, size=(64, 3))
     nodes[:8, 0] = 0; nodes[8:16, 1] = 255; nodes[16:24, 2] = 0
-    want, amb = F.fbp(geom, p, w, nodes=nodes, ambiguity=EPS_K)
+    want, amb = F.fbp(geom, p, w, nodes=nodes, ambiguity=eps_k(geom))
     got_s = got[nodes[:, 2], nodes[:, 1], nodes[:, 0]]
     print(f"fbp full size: raw rel-L2 {rel(got_s, want):.3e}, beyond the allowance {rel_beyond(got_s, want, amb):.3e}")
     assert rel_beyond(got_s, want, amb) <= TOL, (rel(got_s, want), rel_beyond(got_s, want, amb))
