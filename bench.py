@@ -62,13 +62,31 @@ def _config(geom, world=1):
             "parallelism": f"replicas x{world}"}
 
 
+KERNEL_SOURCES = ["forward.cu", "adjoint.cu", "brick.cuh", "oat_internal.h", "plan.cpp"]
+
+
+def kernel_source_hash():
+    """SHA-256 (first 16 hex digits) of the sources of the H / H^T kernels and their plan tables."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1304_2017_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def _counters():
-    """Per-kernel ncu counters committed under profiles/ (None where not measured)."""
+    """Per-kernel ncu counters committed under profiles/ (None where not measured).  They count
+    only while the kernels are the ones profiled: counters.json records the hash of their sources,
+    and a different hash here discards the counters."""
     try:
         with open(os.path.join(ROOT, "profiles", "counters.json")) as f:
-            return {k: v for k, v in json.load(f).items() if not k.startswith("_")}
+            c = json.load(f)
     except (OSError, ValueError):
         return {}
+    if c.get("_kernel_source_hash") != kernel_source_hash():
+        return {}
+    return {k: v for k, v in c.items() if not k.startswith("_")}
 
 
 def l2_read_gbs(dev, mb=48, reps=100):

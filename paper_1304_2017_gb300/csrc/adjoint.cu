@@ -143,6 +143,8 @@ constexpr int kQueue = 64;   // per-warp queue of owned points (power of two, >=
 
 // Scatter one owned point (cell-local weights wx, wy, wz; first node b in the low 16 bits of
 // e.w, the point's shell s within the unit above them) with value wg[s].
+// The eight weights are the products (g uz_or_wz) uy_or_wy ux_or_wx in that order, formed in
+// packed FP32 pairs.
 template <int S1, int S2>
 __device__ __forceinline__ void scatter8(int *shi, unsigned int *slo, float4 e, const float *wg, float wr = 1.f) {
     const float wx = e.x, wy = e.y, wz = e.z;
@@ -150,11 +152,21 @@ __device__ __forceinline__ void scatter8(int *shi, unsigned int *slo, float4 e, 
     const int b = bs & 0xffff;
     const float gq = wg[bs >> 16] * wr;
     const float ux = 1.f - wx, uy = 1.f - wy, uz = 1.f - wz;
-    const float g00 = gq * uz * uy, g01 = gq * uz * wy, g10 = gq * wz * uy, g11 = gq * wz * wy;
-    sadd(shi, slo, b, g00 * ux);           sadd(shi, slo, b + 1, g00 * wx);
-    sadd(shi, slo, b + S1, g01 * ux);      sadd(shi, slo, b + S1 + 1, g01 * wx);
-    sadd(shi, slo, b + S2, g10 * ux);      sadd(shi, slo, b + S2 + 1, g10 * wx);
-    sadd(shi, slo, b + S2 + S1, g11 * ux); sadd(shi, slo, b + S2 + S1 + 1, g11 * wx);
+    const f32x2 Z = mul2(pk2(gq, gq), pk2(uz, wz));          // (g uz, g wz)
+    const f32x2 Y0 = mul2(Z, pk2(uy, uy)), Y1 = mul2(Z, pk2(wy, wy));
+    float g00, g10, g01, g11;
+    upk2(Y0, g00, g10);
+    upk2(Y1, g01, g11);
+    const f32x2 X = pk2(ux, wx);
+    float v0, v1;
+    upk2(mul2(pk2(g00, g00), X), v0, v1);
+    sadd(shi, slo, b, v0);           sadd(shi, slo, b + 1, v1);
+    upk2(mul2(pk2(g01, g01), X), v0, v1);
+    sadd(shi, slo, b + S1, v0);      sadd(shi, slo, b + S1 + 1, v1);
+    upk2(mul2(pk2(g10, g10), X), v0, v1);
+    sadd(shi, slo, b + S2, v0);      sadd(shi, slo, b + S2 + 1, v1);
+    upk2(mul2(pk2(g11, g11), X), v0, v1);
+    sadd(shi, slo, b + S2 + S1, v0); sadd(shi, slo, b + S2 + S1 + 1, v1);
 }
 
 template <int B, int DT, bool AREA>

@@ -155,7 +155,7 @@ __device__ __forceinline__ bool ring_box_ranges(const BrickView &v, const Ring &
 // in three levels:
 //   rings     the units' rings, flattened over its shells, one lane per ring: the ring's azimuth
 //             windows clipped to the brick (ring_windows);
-//   segments  the part of a window that shares one anchor (j >> 5): up to 32 points.  One lane
+//   segments  the part of a window that shares one anchor (j >> ash): up to 32 points.  One lane
 //             per segment computes the anchor and fills a slot (segment_chunk);
 //   points    the segments' points spread evenly over the lanes (segment_point).
 constexpr int kShells = 4;
@@ -192,13 +192,15 @@ struct __align__(16) SegSlot {
     int I[3];            // anchor cell I, relative to the brick's lowest cell L
     float xa, ya;        // anchor local coordinates (hi parts)
     float dphi, dphi_lo;
-    int mp;              // m = j - j_A of the segment's first point | poly << 5 | shell << 6 |
+    int mp;              // m = j - j_A of the segment's first point | shell << 6 |
                          // position of that point in the chunk's candidate list << 8
     float w;             // the ring's point weight over Delta_s^2 (1 with uniform weights)
 };
 
-__device__ __forceinline__ int anchor_segments(int lo, int n) {
-    return n > 0 ? ((lo + n - 1) >> kAnchorShift) - (lo >> kAnchorShift) + 1 : 0;
+// Anchor segments (runs of points sharing an anchor, anchors every 2^sh points) of the index
+// range lo .. lo + n - 1.
+__device__ __forceinline__ int anchor_segments(int lo, int n, int sh) {
+    return n > 0 ? ((lo + n - 1) >> sh) - (lo >> sh) + 1 : 0;
 }
 
 // Lane's ring gidx (none if < 0): its windows [wa0, wa0 + wna) and [wb0, wb0 + wnb) clipped to
@@ -207,14 +209,15 @@ __device__ __forceinline__ int anchor_segments(int lo, int n) {
 __device__ __forceinline__ int ring_windows(const BrickView &v, const Ring *__restrict__ rings, int gidx,
                                             const float O[3], float rb2, const float blo[3], const float bhi[3],
                                             int lane, int &wa0, int &wna, int &wb0, int &wnb, int &sincl) {
-    int a0 = 0, a1 = -1, b0 = 0, b1 = -1;
+    int a0 = 0, a1 = -1, b0 = 0, b1 = -1, sh = 0;
     if (gidx >= 0) {
         const Ring r = rings[gidx];
         ring_box_ranges(v, r, ring_base(O, v.ez, r.h), rb2, blo, bhi, a0, a1, b0, b1);
+        sh = r.ash;
     }
     wa0 = a0; wna = max(0, a1 - a0 + 1);
     wb0 = b0; wnb = max(0, b1 - b0 + 1);
-    int incl = anchor_segments(wa0, wna) + anchor_segments(wb0, wnb);
+    int incl = anchor_segments(wa0, wna, sh) + anchor_segments(wb0, wnb, sh);
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int t = __shfl_up_sync(0xffffffffu, incl, o);
@@ -252,15 +255,16 @@ __device__ __forceinline__ int segment_chunk(const Xdcr *__restrict__ xq, const 
     cshell = __shfl_sync(0xffffffffu, rshell, 0);
     if (ONE_SHELL) take = take && rshell == cshell;
     used = __popc(__ballot_sync(0xffffffffu, take));
-    int cnt = 0, j0 = 0, t = 0;
+    int cnt = 0, j0 = 0, t = 0, sh = 0;
     if (take) {
-        const int nsa = anchor_segments(ra0, rna), nsb = anchor_segments(rb0, rnb);
+        sh = __ldg(&rings[rg_idx].ash);
+        const int nsa = anchor_segments(ra0, rna, sh), nsb = anchor_segments(rb0, rnb, sh);
         const int sg = g - (rincl - nsa - nsb);
         int lo, hi;
-        if (sg < nsa) { t = (ra0 >> kAnchorShift) + sg; lo = ra0; hi = ra0 + rna - 1; }
-        else { t = (rb0 >> kAnchorShift) + (sg - nsa); lo = rb0; hi = rb0 + rnb - 1; }
-        j0 = max(lo, t << kAnchorShift);
-        cnt = min(hi, (t << kAnchorShift) + kAnchorMask) - j0 + 1;
+        if (sg < nsa) { t = (ra0 >> sh) + sg; lo = ra0; hi = ra0 + rna - 1; }
+        else { t = (rb0 >> sh) + (sg - nsa); lo = rb0; hi = rb0 + rnb - 1; }
+        j0 = max(lo, t << sh);
+        cnt = min(hi, (t << sh) + (1 << sh) - 1) - j0 + 1;
     }
     int incl = cnt;
 #pragma unroll
@@ -279,7 +283,7 @@ __device__ __forceinline__ int segment_chunk(const Xdcr *__restrict__ xq, const 
         for (int d = 0; d < 3; ++d) { sl.f[d] = fr[d]; sl.I[d] = I[d] - L[d]; }
         sl.xa = xy.x; sl.ya = xy.z;
         sl.dphi = rg.dphi; sl.dphi_lo = rg.dphi_lo;
-        sl.mp = (j0 - (t << kAnchorShift)) | (rg.poly << 5) | (rshell << 6) | ((incl - cnt) << 8);
+        sl.mp = (j0 - (t << sh)) | (rshell << 6) | ((incl - cnt) << 8);
         sl.w = ring_w ? __ldg(ring_w + rg_idx) : 1.f;
     }
     my_start = cnt > 0 ? incl - cnt : 0x7fffffff;
@@ -301,8 +305,7 @@ __device__ __forceinline__ int segment_point(const SegSlot *ws, int f, int lane,
     if (cidx >= total) return -1;
     const SegSlot &sl = ws[before - 1 + __popc(inside & ((2u << lane) - 1u))];
     const int mp = sl.mp;
-    const float3 R = anchor_offset(sl.f, sl.xa, sl.ya, ex, ey, sl.dphi, sl.dphi_lo, (mp >> 5) & 1,
-                                   (mp & kAnchorMask) + (cidx - (mp >> 8)));
+    const float3 R = anchor_offset(sl.f, sl.xa, sl.ya, ex, ey, sl.dphi, sl.dphi_lo, (mp & 31) + (cidx - (mp >> 8)));
     const float fx = floorf(R.x), fy = floorf(R.y), fz = floorf(R.z);
     lc[0] = sl.I[0] + (int)fx; lc[1] = sl.I[1] + (int)fy; lc[2] = sl.I[2] + (int)fz;
     w[0] = __fsub_rn(R.x, fx); w[1] = __fsub_rn(R.y, fy); w[2] = __fsub_rn(R.z, fz);

@@ -9,9 +9,10 @@
 //        FP32 fraction.  A voxel at offset delta from the centre is at distance D + dD with
 //          dD = (2 D u.delta + |delta|^2) / (D + sqrt(D^2 + 2 D u.delta + |delta|^2))
 //        (u the unit vector from the transducer to the centre): every FP32 quantity stays
-//        small, so k~ = K + dD ds / (c dt) keeps a few 1e-6 of a sample (measured against FP64
-//        through oat_fbp_sample_positions; the SFU square root and reciprocal each get one Newton
-//        step, which halves the worst case).  Per term, with w = k~ - k and
+//        small, so k~ = K + dD ds / (c dt) is good to about 2e-6 grid units of distance (worst
+//        case; 2.5e-7 rms), measured against FP64 through oat_fbp_sample_positions: the roundings of
+//        the FP32 offset terms dominate, not the SFU square root and reciprocal (a Newton step on
+//        each changed nothing measurable).  Per term, with w = k~ - k and
 //        tau = k~ + t_min / dt,
 //          {..} = 0.5 (p_{k+1} - p_k) + (p_k + w (p_{k+1} - p_k)) / tau
 //        (the braces of Eq. disfbp rewritten), summed with compensation over a tile and in
@@ -31,30 +32,6 @@ constexpr int kFbpB = 8;
 constexpr int kFbpThreads = kFbpB * kFbpB * kFbpB / 2;   // two voxels per thread
 constexpr int kFbpTile = 256;                           // transducers per tile, one per thread
 
-// Two floats in one 64-bit register for the packed FP32 instructions of sm_100+
-// (add / mul / fma .rn.f32x2 round like their scalar forms, lane by lane).
-typedef unsigned long long f32x2;
-__device__ __forceinline__ f32x2 pk2(float a, float b) {
-    f32x2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void upk2(f32x2 r, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
-__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
-    f32x2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
-    f32x2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
-    f32x2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
 static_assert(kFbpTile == kFbpThreads, "one transducer set-up per thread and tile");
 
 struct FbpArgs {
@@ -152,21 +129,12 @@ __device__ __forceinline__ void fbp_kpos(const FbpQ &Q, float dx, float dy, f32x
     const f32x2 TT = fma2(pk2(td, td), UD, DD);
     const f32x2 DQ = pk2(Q.D, Q.D);
     const f32x2 S2 = fma2(DQ, DQ, TT);
-    const f32x2 M1 = pk2(-1.f, -1.f);
     float s2a, s2b;
     upk2(S2, s2a, s2b);
-    // sqrt(S2) from the SFU reciprocal square root, then one Newton step on its residual
-    const f32x2 RS = pk2(rsqrtf(s2a), rsqrtf(s2b));
-    f32x2 SQ = mul2(S2, RS);
-    SQ = fma2(mul2(RS, pk2(0.5f, 0.5f)), fma2(mul2(SQ, M1), SQ, S2), SQ);
-    const f32x2 DEN = add2(DQ, SQ);
+    const f32x2 DEN = add2(DQ, mul2(S2, pk2(rsqrtf(s2a), rsqrtf(s2b))));
     float dna, dnb;
     upk2(DEN, dna, dnb);
-    // 1 / DEN from the SFU reciprocal, then one Newton step (the SFU's 2-ulp error would move k~
-    // by up to ~4e-6 of a sample at 450 grid units)
-    f32x2 RC = pk2(__fdividef(1.f, dna), __fdividef(1.f, dnb));
-    RC = fma2(RC, fma2(mul2(DEN, M1), RC, pk2(1.f, 1.f)), RC);
-    DDD = mul2(TT, RC);   // distance - D
+    DDD = mul2(TT, pk2(__fdividef(1.f, dna), __fdividef(1.f, dnb)));   // distance - D
     KF = fma2(DDD, pk2(sk, sk), pk2(Q.kfrac, Q.kfrac));
 }
 

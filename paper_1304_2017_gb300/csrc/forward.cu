@@ -85,6 +85,24 @@ __device__ __forceinline__ void flush_shell(float s, float e, double scale, int 
     }
 }
 
+// Trilinear interpolation (Eq. expfunI) at weights w of the cell whose first node is sp (node
+// strides 1, S1, S2): x-lerps of the (z, z + 1) corner pairs side by side, then the y-lerps of
+// the two z planes side by side, then z.  Each lerp is fma(w, b - a, a), as a scalar evaluation
+// would round it.
+template <int S1, int S2>
+__device__ __forceinline__ float trilinear(const float *sp, const float w[3]) {
+    const f32x2 M1 = pk2(-1.f, -1.f);
+    const f32x2 A0 = pk2(sp[0], sp[S2]), A1 = pk2(sp[1], sp[S2 + 1]);
+    const f32x2 B0 = pk2(sp[S1], sp[S2 + S1]), B1 = pk2(sp[S1 + 1], sp[S2 + S1 + 1]);
+    const f32x2 WX = pk2(w[0], w[0]);
+    const f32x2 CA = fma2(WX, fma2(A0, M1, A1), A0);   // (c00, c10)
+    const f32x2 CB = fma2(WX, fma2(B0, M1, B1), B0);   // (c01, c11)
+    const f32x2 E = fma2(pk2(w[1], w[1]), fma2(CA, M1, CB), CA);
+    float e0, e1;
+    upk2(E, e0, e1);
+    return fmaf(w[2], e1 - e0, e0);
+}
+
 // COUNT: instead of interpolating, count the points each brick owns (the bricks tile the cells
 // [-1, n-1]^3, so the total is the number of lattice points whose stencil touches the grid).
 template <int B, bool COUNT, bool AREA>
@@ -159,9 +177,11 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_brick_gather(FwdArgs a) {
         int p0, p1, p2;
         const int T = unit_shells(n, lane, p0, p1, p2);
         if (T == 0) continue;
-        // chunks hold one shell each (in shell order): a compensated FP32 sum per lane, reduced
-        // over the warp and added as a fixed-point integer when the shell changes
-        float acc = 0.f, err = 0.f;
+        // chunks hold one shell each (in shell order): a Kahan-compensated FP32 sum per lane (sum
+        // acc, compensation kc: the sum is acc - kc), reduced over the warp with compensation and
+        // added as a fixed-point integer when the shell changes.  H is a difference of neighbouring
+        // shell sums (D), which cancels by up to a few digits, so the sums keep more than FP32.
+        float acc = 0.f, kc = 0.f;
         int cur = -1;
         for (int ib = 0; ib < T; ib += 32) {
             int shell;
@@ -173,8 +193,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_brick_gather(FwdArgs a) {
                 const int total = segment_chunk<true>(a.t.xd + q, a.t.rings, a.t.anchors, AREA ? a.t.ring_w : nullptr, gidx, shell, a.O, a.O_lo, L,
                                                       sc, S, lane, wa0, wna, wb0, wnb, sincl, ws, my_start, used, csh);
                 if (csh != cur) {
-                    if (!COUNT && cur >= 0) flush_shell(acc, err, scale, lane, a.gacc + (size_t)q * a.K + kb + cur);
-                    acc = 0.f; err = 0.f; cur = csh;
+                    if (!COUNT && cur >= 0) flush_shell(acc, -kc, scale, lane, a.gacc + (size_t)q * a.K + kb + cur);
+                    acc = 0.f; kc = 0.f; cur = csh;
                 }
                 for (int f = 0; f < total; f += 32) {
                     int lc[3];
@@ -183,16 +203,17 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_brick_gather(FwdArgs a) {
                     if ((unsigned)lc[0] < (unsigned)E[0] && (unsigned)lc[1] < (unsigned)E[1] && (unsigned)lc[2] < (unsigned)E[2]) {
                         if (COUNT) { ++owned; continue; }
                         const float *sp = sv + lc[2] * S2 + lc[1] * S1 + lc[0];
-                        const float c00 = lerp1(sp[0], sp[1], w[0]), c01 = lerp1(sp[S1], sp[S1 + 1], w[0]);
-                        const float c10 = lerp1(sp[S2], sp[S2 + 1], w[0]), c11 = lerp1(sp[S2 + S1], sp[S2 + S1 + 1], w[0]);
-                        const float v = lerp1(lerp1(c00, c01, w[1]), lerp1(c10, c11, w[1]), w[2]);
-                        kadd(acc, err, AREA ? wr * v : v);
+                        const float v = trilinear<S1, S2>(sp, w);
+                        const float y = __fsub_rn(AREA ? wr * v : v, kc);
+                        const float t = __fadd_rn(acc, y);
+                        kc = __fsub_rn(__fsub_rn(t, acc), y);
+                        acc = t;
                     }
                 }
                 __syncwarp();
             }
         }
-        if (!COUNT && cur >= 0) flush_shell(acc, err, scale, lane, a.gacc + (size_t)q * a.K + kb + cur);
+        if (!COUNT && cur >= 0) flush_shell(acc, -kc, scale, lane, a.gacc + (size_t)q * a.K + kb + cur);
     }
     if (COUNT) {
 #pragma unroll

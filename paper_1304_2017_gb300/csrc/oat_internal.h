@@ -26,17 +26,18 @@ namespace oat {
 // (e_x, e_y, e_z) is the transducer's local frame (Appendix).
 //
 // h and dphi are also kept as unevaluated sums of two floats (hi + lo, |lo| <= ulp(hi) / 2),
-// for the anchors below.  Anchor t of the ring is the point j = 32 t; its local coordinates
-// (a cos(32 t dphi), a sin(32 t dphi)) are table entries aoff + t, also as float pairs.
-constexpr int kAnchorShift = 5;                      // one anchor every 32 points of a ring
-constexpr int kAnchorMask = (1 << kAnchorShift) - 1;
+// for the anchors below.  The ring's anchors sit every 2^ash points, ash the largest value <= 5
+// with 2^ash dphi <= 1 (so that a point is at most 1 rad of azimuth from its anchor): anchor t
+// is the point j = t 2^ash, its local coordinates (a cos(j dphi), a sin(j dphi)) are table entry
+// aoff + t, also as float pairs.
+constexpr int kMaxAnchorShift = 5;                   // at most 32 points per anchor
 
 struct __align__(16) Ring {
     float h, a, dphi;
     int nj;
     float h_lo, dphi_lo;
     int aoff;                 // first anchor of the ring in the anchor table
-    int poly;                 // 1: offsets by Taylor polynomials (32 dphi <= 1), 0: by sincosf
+    int ash;                  // anchor spacing 2^ash points (0 .. 5)
 };
 
 // Per-transducer record: local frame (float pairs hi + lo) and |r_q| / Delta_s, radius class.
@@ -210,46 +211,64 @@ __device__ __forceinline__ void anchor_point(const float Oh[3], const float Ol[3
     }
 }
 
-// sin(d) and cos(d) - 1 for |d| <= 1 from their Taylor series (through d^11 and d^12: the
-// first omitted terms are below 2e-10), Horner form in FP32.
-__device__ __forceinline__ void taylor_sin_cosm1(float d, float &sd, float &cm) {
-    constexpr float s3 = (float)(-1.0 / 6.0), s5 = (float)(1.0 / 120.0), s7 = (float)(-1.0 / 5040.0);
-    constexpr float s9 = (float)(1.0 / 362880.0), s11 = (float)(-1.0 / 39916800.0);
-    constexpr float c2 = -0.5f, c4 = (float)(1.0 / 24.0), c6 = (float)(-1.0 / 720.0), c8 = (float)(1.0 / 40320.0);
-    constexpr float c10 = (float)(-1.0 / 3628800.0), c12 = (float)(1.0 / 479001600.0);
-    const float d2 = __fmul_rn(d, d);
-    float p = fmaf(d2, s11, s9);
-    p = fmaf(d2, p, s7);
-    p = fmaf(d2, p, s5);
-    p = fmaf(d2, p, s3);
-    sd = fmaf(__fmul_rn(d, d2), p, d);
-    float c = fmaf(d2, c12, c10);
-    c = fmaf(d2, c, c8);
-    c = fmaf(d2, c, c6);
-    c = fmaf(d2, c, c4);
-    c = fmaf(d2, c, c2);
-    cm = __fmul_rn(d2, c);
+// Two floats in one 64-bit register for the packed FP32 instructions of sm_100+: add / mul /
+// fma .rn.f32x2 round like their scalar forms, lane by lane, so a packed evaluation gives the
+// bits of the scalar one at about half the issued instructions.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(f32x2 r, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
 }
 
-// Point m = j - j_A (0 <= m < 32) of a ring relative to its anchor's cell: P - I.
-// (xa, ya): the anchor's local coordinates (hi parts); poly: the ring's flag (32 dphi <= 1).
+// Point m = j - j_A (0 <= m < 2^ash <= 32) of a ring relative to its anchor's cell: P - I.
+// (xa, ya): the anchor's local coordinates (hi parts).  The rotation delta = m dphi (|delta| <=
+// 1 by the choice of the anchor spacing) enters through sin(delta) and cos(delta) - 1 from their
+// Taylor series through delta^11 and delta^12 (the first omitted terms are below 2e-10), Horner
+// form in FP32, the two series side by side in packed FP32 pairs.  Then
+//   dx = x_A (cos delta - 1) - y_A sin delta,  dy = y_A (cos delta - 1) + x_A sin delta,
+//   P - I = f + dx e_x + dy e_y.
 __device__ __forceinline__ float3 anchor_offset(const float f[3], float xa, float ya, const float ex[3],
-                                                const float ey[3], float dphi, float dphi_lo, int poly, int m) {
+                                                const float ey[3], float dphi, float dphi_lo, int m) {
     const float mf = __int2float_rn(m);
     const float d = fmaf(mf, dphi_lo, __fmul_rn(mf, dphi));
-    float sd, cm;
-    if (poly) {
-        taylor_sin_cosm1(d, sd, cm);
-    } else {
-        float c;
-        sincosf(d, &sd, &c);
-        cm = __fsub_rn(c, 1.f);
-    }
-    const float dx = fmaf(-ya, sd, __fmul_rn(xa, cm));
-    const float dy = fmaf(xa, sd, __fmul_rn(ya, cm));
-    return make_float3(fmaf(dy, ey[0], fmaf(dx, ex[0], f[0])),
-                       fmaf(dy, ey[1], fmaf(dx, ex[1], f[1])),
-                       fmaf(dy, ey[2], fmaf(dx, ex[2], f[2])));
+    const float d2 = __fmul_rn(d, d);
+    const f32x2 D2 = pk2(d2, d2);
+    // (sin series, cos series): coefficients of delta^11 / delta^12 down to delta^3 / delta^4
+    f32x2 P = fma2(D2, pk2((float)(-1.0 / 39916800.0), (float)(1.0 / 479001600.0)),
+                   pk2((float)(1.0 / 362880.0), (float)(-1.0 / 3628800.0)));
+    P = fma2(D2, P, pk2((float)(-1.0 / 5040.0), (float)(1.0 / 40320.0)));
+    P = fma2(D2, P, pk2((float)(1.0 / 120.0), (float)(-1.0 / 720.0)));
+    P = fma2(D2, P, pk2((float)(-1.0 / 6.0), (float)(1.0 / 24.0)));
+    float ps, pc;
+    upk2(P, ps, pc);
+    const float sd = fmaf(__fmul_rn(d, d2), ps, d);
+    const float cm = __fmul_rn(d2, fmaf(d2, pc, -0.5f));
+    // (dx, dy) = (xa cm - ya sd, ya cm + xa sd)
+    const f32x2 DXY = fma2(pk2(-ya, xa), pk2(sd, sd), mul2(pk2(xa, ya), pk2(cm, cm)));
+    float dx, dy;
+    upk2(DXY, dx, dy);
+    f32x2 R01 = fma2(pk2(dx, dx), pk2(ex[0], ex[1]), pk2(f[0], f[1]));
+    R01 = fma2(pk2(dy, dy), pk2(ey[0], ey[1]), R01);
+    float r0, r1;
+    upk2(R01, r0, r1);
+    return make_float3(r0, r1, fmaf(dy, ey[2], fmaf(dx, ex[2], f[2])));
 }
 
 // Approximate ring centre B = O + h e_z in FP32 (azimuth windows only, which carry margins).

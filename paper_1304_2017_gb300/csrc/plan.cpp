@@ -136,7 +136,7 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
     for (int q = 0; q < Q; ++q) xd[q].cls = cls_of[rs[q]];
 
     // shell lattice per (class, k): rings i < N_i with N_j points each, and the anchors of every
-    // ring: points j = 32 t, local coordinates a (cos(j dphi), sin(j dphi)) as float pairs
+    // ring: points j = t 2^ash, local coordinates a (cos(j dphi), sin(j dphi)) as float pairs
     const int C = p->n_cls;
     std::vector<Ring> rings;
     std::vector<float> ring_w;          // exact strip areas: point weight / Delta_s^2 per ring
@@ -176,16 +176,19 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
                 rr.a = (float)a;
                 split(dph, rr.dphi, rr.dphi_lo);
                 rr.nj = nj;
-                rr.poly = (32.0 * dph <= 1.0) ? 1 : 0;
+                // anchors every 2^ash points, the longest run whose rotation stays within 1 rad
+                int ash = kMaxAnchorShift;
+                while (ash > 0 && (double)(1 << ash) * dph > 1.0) --ash;
+                rr.ash = ash;
                 rr.aoff = (int)anchors.size();
-                if (nj == 0) { rr.dphi = 0.f; rr.dphi_lo = 0.f; rr.a = 0.f; rr.poly = 1; }
-                const int na = (nj + kAnchorMask) >> kAnchorShift;
+                if (nj == 0) { rr.dphi = 0.f; rr.dphi_lo = 0.f; rr.a = 0.f; rr.ash = kMaxAnchorShift; }
+                const int na = nj > 0 ? ((nj + (1 << rr.ash) - 1) >> rr.ash) : 0;
                 if (anchors.size() + (size_t)na >= (size_t)INT32_MAX) {
                     delete p;
                     return set_error(OAT_ERR_UNSUPPORTED, "oat_plan_create: lattice tables exceed 2^31 anchors");
                 }
                 for (int tt = 0; tt < na; ++tt) {
-                    const double phi = (double)(tt << kAnchorShift) * dph;
+                    const double phi = (double)(tt << rr.ash) * dph;
                     float4 e;
                     split(a * std::cos(phi), e.x, e.y);
                     split(a * std::sin(phi), e.z, e.w);
@@ -250,10 +253,25 @@ int plan_create(const oat_geometry *gin, int device, Plan **out) {
         }
         const double rb = 0.5 * std::sqrt(diag2) + 0.05;
         bc.kspan = (int)std::ceil(2.0 * rb / (g.c_mm_per_us * p->dt / ds)) + 2;
-        const long long target = (long long)p->n_sm * 8;
-        long long chunks = std::max(1LL, std::min<long long>(Q, (target + bricks - 1) / bricks));
+        // transducer chunks per brick: at least 8 work items per SM, and as few chunks as leave at
+        // most 2 % of the last wave of work items idle (one block per SM at a time)
+        const long long sms = p->n_sm;
+        const long long c0 = std::max(1LL, std::min<long long>(Q, (sms * 8 + bricks - 1) / bricks));
+        auto items_of = [&](long long c) {
+            const long long qc = (Q + c - 1) / c;
+            return bricks * ((Q + qc - 1) / qc);
+        };
+        auto waste = [&](long long c) {
+            const long long it = items_of(c);
+            return (double)(((it + sms - 1) / sms) * sms) / (double)it - 1.0;
+        };
+        long long chunks = c0;
+        for (long long c = c0; c <= std::min<long long>(Q, 8 * c0); ++c) {
+            if (waste(c) <= 0.02) { chunks = c; break; }
+            if (waste(c) < waste(chunks)) chunks = c;
+        }
         bc.qchunk = (int)((Q + chunks - 1) / chunks);
-        bc.items = bricks * ((Q + bc.qchunk - 1) / bc.qchunk);
+        bc.items = items_of(chunks);
         bc.smem = node_bytes * (size_t)(B + 1) * (B + 1) * (B + 1);
     };
     tile(p->fwd, kBF, sizeof(float));

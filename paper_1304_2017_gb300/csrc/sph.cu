@@ -71,31 +71,7 @@ struct SphArgs {
     float sig_hi, sig_lo, df_hi, df_lo, inv2pids;
 };
 
-// Two floats in one 64-bit register, operated on by the packed FP32 instructions of sm_100+
-// (add / mul / fma .rn.f32x2: each rounds like its scalar form, lane by lane).
-typedef unsigned long long f32x2;
-
-__device__ __forceinline__ f32x2 pk2(float a, float b) {
-    f32x2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void upk2(f32x2 r, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
-__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
-    f32x2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
-    f32x2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
-    f32x2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
+// Packed FP32 pairs (f32x2, pk2, upk2, add2, mul2, fma2) come from oat_internal.h.
 
 // (ph + pl) ~ (ah + al)(bh + bl), the product's rounding error from an FMA, al bl dropped.
 __device__ __forceinline__ void pmul(float ah, float al, float bh, float bl, float &ph, float &pl) {

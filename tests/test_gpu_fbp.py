@@ -48,11 +48,11 @@ def rel_beyond(got, want, amb):
     return float(np.linalg.norm(d) / np.linalg.norm(want))
 
 
-# The kernel's k~ error is a distance error: at most KT_GRID grid units (measured by
-# test_fbp_sample_position_accuracy on every small case and on sampled pairs of the 256^3 /
-# 23,040-transducer scan), i.e. KT_GRID ds / (c dt) samples.  The window of the integer-crossing
-# allowance is twice that bound.
-KT_GRID = 1.5e-6
+# The kernel's k~ error is a distance error: measured by test_fbp_sample_position_accuracy on
+# every small case and on sampled pairs of the 256^3 / 23,040-transducer scan at 1.1e-6 to 1.9e-6
+# grid units at most (rms 2.5e-7), bounded here by KT_GRID grid units, i.e. KT_GRID ds / (c dt)
+# samples.  The window of the integer-crossing allowance is twice that bound.
+KT_GRID = 2.2e-6
 
 
 def kt_max(geom):
