@@ -13,6 +13,7 @@ problem (the operator needs no exchange); the value is the sum over ranks.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import dataclasses
 import json
 import os
@@ -421,6 +422,48 @@ def run_learned(args):
     print(json.dumps(out), flush=True)
 
 
+def run_conv(args):
+    """One 3x3x3 convolution of the warm start's U-Net on the tensor cores (oat_conv3d_bf16,
+    tcgen05.mma): 128^3 voxels, 64 -> 64 channels (the bottleneck layer of a 512^3 input), BF16
+    in and out, FP32 accumulation; TFLOP/s (2 x 27 x cin x cout FLOP per voxel) against the
+    measured dense BF16 peak, CUDA events around K timed calls after W untimed ones."""
+    import torch
+    from paper_1304_2017_gb300 import unet
+    torch.cuda.set_device(0)
+    n, cin, cout = args.conv_size, 64, 64
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.randn((n, n, n, cin), device="cuda", generator=g).to(torch.bfloat16)
+    w = (0.05 * torch.randn((27, cout, cin), device="cuda", generator=g)).to(torch.bfloat16)
+    b = torch.zeros(cout, device="cuda")
+    y = torch.empty((n, n, n, cout), dtype=torch.bfloat16, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+
+    def call():
+        unet._call("oat_conv3d_bf16", n, n, n, cin, cout, unet._p(x), unet._p(w), unet._p(b), 1, unet._p(y),
+                   ctypes.c_void_p(s))
+    for _ in range(args.warmup):
+        call()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    unet._call("oat_unet_check")
+    sec = e0.elapsed_time(e1) * 1e-3 / args.steps
+    flop = 2.0 * 27 * cin * cout * n ** 3
+    peaks, src = _peaks()
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    line = {"metric": "U-Net 3x3x3 convolution TFLOP/s (tcgen05, BF16 in, FP32 accumulation)",
+            "value": flop / sec * 1e-12, "unit": "TFLOP/s", "seconds_per_conv": sec, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"{n}^3 voxels, {cin} -> {cout} channels, channels last"},
+            "roofline": {"bound": "tensor", "achieved": flop / sec * 1e-12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flop / sec * 1e-12 / peak, "peak_source": f"{src} dense BF16 burst (cuBLAS)"}}
+    print(json.dumps(line), flush=True)
+
+
 def run_capture():
     """The workload restricted to 64 transducers (rings 10, 30, 50, 64, 70, 90, 110, 120 x views
     0, 20, ..., 140): 2.9e9 interpolations per operator, ~2 GB on the device."""
@@ -466,6 +509,9 @@ def main():
     ap.add_argument("--sph", action="store_true",
                     help="spherical-voxel model H_sph + H_sph^T on the paper's 210 x 210 x 440 grid")
     ap.add_argument("--sph-transducers", type=int, default=0, help="--sph on this many transducers (0: all)")
+    ap.add_argument("--conv", action="store_true",
+                    help="one tensor-core 3x3x3 convolution of the U-Net (64 -> 64 channels) on a --conv-size^3 grid")
+    ap.add_argument("--conv-size", type=int, default=128)
     ap.add_argument("--capture", action="store_true",
                     help="small case for ncu captures: the 256^3 workload on 64 transducers, H and H^T twice")
     args = ap.parse_args()
@@ -473,6 +519,8 @@ def main():
         return run_reference(args)
     if args.capture:
         return run_capture()
+    if args.conv:
+        return run_conv(args)
     if args.learned:
         return run_learned(args)
     if args.pls:

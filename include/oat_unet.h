@@ -17,10 +17,17 @@
 extern "C" {
 #endif
 
-/* y = act(b + conv3x3x3(x, w)) on the tensor cores (BF16 in, FP32 accumulation, BF16 out);
- * cin a multiple of 16, cout 16, 32, 48, 64 or 96; relu != 0 applies max(0, .); bias may be NULL. */
+/* y = act(b + conv3x3x3(x, w)) on the 5th-generation tensor cores: tcgen05.mma, BF16 in, FP32
+ * accumulation in tensor memory, BF16 out; operands staged in shared memory by TMA.
+ * cin a multiple of 16 up to 96, cout 16, 32, 48, 64 or 96; relu != 0 applies max(0, .); bias
+ * may be NULL.  x, w and y must be 16-byte aligned (OAT_ERR_INVALID_ARG otherwise). */
 int oat_conv3d_bf16(int nx, int ny, int nz, int cin, int cout, const void *x, const void *w, const float *bias, int relu,
                     void *y, void *stream);
+
+/* Synchronous status of the tensor-core convolutions launched so far: OAT_OK, or OAT_ERR_CUDA if
+ * one of them gave up waiting on its copy / MMA pipeline (a bounded wait ran out, about a second;
+ * its output is then undefined).  Reading the status clears it. */
+int oat_unet_check(void);
 
 /* wf[tap][ci][co] = w[26 - tap][co][ci]: with it, oat_conv3d_bf16(g, wf) is the input gradient. */
 int oat_conv3d_flip_weights(int cin, int cout, const void *w, void *wf, void *stream);

@@ -18,7 +18,7 @@ LIB = os.path.join(PKG, "liboat.so")
 ROOT = os.path.dirname(PKG)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["abi.cpp", "plan.cpp", "forward.cu", "adjoint.cu", "recon.cu", "unet.cu", "probe.cu", "fbp.cu", "eir.cu", "sph.cu"]
+SOURCES = ["abi.cpp", "plan.cpp", "forward.cu", "adjoint.cu", "recon.cu", "unet.cu", "conv_tc.cu", "probe.cu", "fbp.cu", "eir.cu", "sph.cu"]
 
 
 def nvcc() -> str:

@@ -147,6 +147,11 @@ int launch_apply_d_eir(Plan &p, void *data, cudaStream_t s);
 int launch_eir_t(Plan &p, const void *y, float *z, cudaStream_t s);
 int launch_fbp(Plan &p, const void *data, float *vol, cudaStream_t s);
 int launch_fbp_kpos(Plan &p, const int *nodes, const int *qs, int n, double *out, cudaStream_t s);
+
+// tensor-core convolution of the learned warm start (conv_tc.cu)
+int launch_conv3d_tc(int nx, int ny, int nz, int cin, int cout, const void *x, const void *w, const float *bias, int relu,
+                     void *y, cudaStream_t s);
+int conv_tc_check();
 int set_adjoint_attributes();
 int set_forward_attributes();
 size_t forward_smem_bytes();

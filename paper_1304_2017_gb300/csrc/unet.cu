@@ -4,13 +4,10 @@
 // w[tap][cout][cin], tap = (dz * 3 + dy) * 3 + dx for offsets (dz - 1, dy - 1, dx - 1), zero
 // padding ('same').
 //
-// k_conv3d: implicit GEMM on the tensor cores.  Rows are 16 consecutive voxels along x (one
-// warp), columns the output channels, the reduction runs over 27 taps x input channels in
-// steps of 16; each step is one mma.sync.m16n8k16 (BF16 inputs, FP32 accumulation) per 8
-// output channels.  Epilogue: + bias, optional ReLU, BF16 store.  The input gradient of a
-// 'same' 3x3x3 convolution is the same convolution of the output gradient with the kernel
-// flipped in space and transposed in channels, so the same kernel serves the backward pass
-// (k_flip_weights builds that kernel).
+// The convolution itself (oat_conv3d_bf16) runs on the 5th-generation tensor cores in
+// conv_tc.cu.  The input gradient of a 'same' 3x3x3 convolution is the same convolution of the
+// output gradient with the kernel flipped in space and transposed in channels, so the same kernel
+// serves the backward pass (k_flip_weights builds that kernel).
 // k_conv3d_wgrad: weight and bias gradients on the FP32 cores (training only).
 #include <cuda_bf16.h>
 
@@ -23,61 +20,6 @@
 namespace oat {
 
 typedef __nv_bfloat16 bf16;
-
-__device__ __forceinline__ unsigned ld_pair(const bf16 *p) { return *reinterpret_cast<const unsigned *>(p); }
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
-                                         unsigned b0, unsigned b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-template <int COUT>
-__global__ void __launch_bounds__(128) k_conv3d(int nx, int ny, int nz, int cin, const bf16 *__restrict__ x,
-                                                const bf16 *__restrict__ w, const float *__restrict__ bias, int relu,
-                                                bf16 *__restrict__ y) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int x0 = blockIdx.x * 64 + warp * 16, yy = blockIdx.y, zz = blockIdx.z;
-    const int g = lane >> 2, kq = (lane & 3) * 2;
-    float acc[COUT / 8][4];
-#pragma unroll
-    for (int n = 0; n < COUT / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-    if (x0 < nx) {
-        for (int tap = 0; tap < 27; ++tap) {
-            const int zs = zz + tap / 9 - 1, ys = yy + (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-            if (zs < 0 || zs >= nz || ys < 0 || ys >= ny) continue;
-            const int xa = x0 + g + dx, xb = xa + 8;
-            const bool oa = xa >= 0 && xa < nx, ob = xb >= 0 && xb < nx;
-            const size_t row = ((size_t)zs * ny + ys) * nx;
-            const bf16 *pa = x + (row + (oa ? xa : 0)) * cin + kq;
-            const bf16 *pb = x + (row + (ob ? xb : 0)) * cin + kq;
-            const bf16 *wt = w + ((size_t)tap * COUT + g) * cin + kq;
-            for (int c = 0; c < cin; c += 16) {
-                const unsigned a0 = oa ? ld_pair(pa + c) : 0u, a1 = ob ? ld_pair(pb + c) : 0u;
-                const unsigned a2 = oa ? ld_pair(pa + c + 8) : 0u, a3 = ob ? ld_pair(pb + c + 8) : 0u;
-#pragma unroll
-                for (int n = 0; n < COUT / 8; ++n) {
-                    const bf16 *wp = wt + (size_t)n * 8 * cin + c;
-                    mma_bf16(acc[n], a0, a1, a2, a3, ld_pair(wp), ld_pair(wp + 8));
-                }
-            }
-        }
-    }
-    const size_t base = ((size_t)zz * ny + yy) * nx;
-#pragma unroll
-    for (int n = 0; n < COUT / 8; ++n) {
-        const int co = n * 8 + kq;
-        const float b0 = bias ? bias[co] : 0.f, b1 = bias ? bias[co + 1] : 0.f;
-        float v0 = acc[n][0] + b0, v1 = acc[n][1] + b1, v2 = acc[n][2] + b0, v3 = acc[n][3] + b1;
-        if (relu) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); v2 = fmaxf(v2, 0.f); v3 = fmaxf(v3, 0.f); }
-        const int xa = x0 + g, xb = xa + 8;
-        if (xa < nx) *reinterpret_cast<__nv_bfloat162 *>(y + (base + xa) * COUT + co) = __floats2bfloat162_rn(v0, v1);
-        if (xb < nx) *reinterpret_cast<__nv_bfloat162 *>(y + (base + xb) * COUT + co) = __floats2bfloat162_rn(v2, v3);
-    }
-}
 
 // wf[tap][ci][co] = w[26 - tap][co][ci]: kernel of the input gradient
 __global__ void k_flip_weights(int cin, int cout, const bf16 *__restrict__ w, bf16 *__restrict__ wf) {
@@ -305,20 +247,13 @@ extern "C" {
 
 int oat_conv3d_bf16(int nx, int ny, int nz, int cin, int cout, const void *x, const void *w, const float *bias, int relu,
                     void *y, void *stream) {
-    if (nx < 1 || ny < 1 || nz < 1 || cin < 16 || cin % 16 || !x || !w || !y ||
+    if (nx < 1 || ny < 1 || nz < 1 || cin < 16 || cin > 96 || cin % 16 || !x || !w || !y ||
         (cout != 16 && cout != 32 && cout != 48 && cout != 64 && cout != 96))
-        return set_error(OAT_ERR_INVALID_ARG, "oat_conv3d_bf16: need cin a multiple of 16, cout in {16, 32, 48, 64, 96}");
-    const dim3 grid((nx + 63) / 64, ny, nz);
-    cudaStream_t s = (cudaStream_t)stream;
-    const bf16 *xb = (const bf16 *)x, *wb = (const bf16 *)w;
-    bf16 *yb = (bf16 *)y;
-    if (cout == 16) k_conv3d<16><<<grid, 128, 0, s>>>(nx, ny, nz, cin, xb, wb, bias, relu, yb);
-    else if (cout == 32) k_conv3d<32><<<grid, 128, 0, s>>>(nx, ny, nz, cin, xb, wb, bias, relu, yb);
-    else if (cout == 48) k_conv3d<48><<<grid, 128, 0, s>>>(nx, ny, nz, cin, xb, wb, bias, relu, yb);
-    else if (cout == 64) k_conv3d<64><<<grid, 128, 0, s>>>(nx, ny, nz, cin, xb, wb, bias, relu, yb);
-    else k_conv3d<96><<<grid, 128, 0, s>>>(nx, ny, nz, cin, xb, wb, bias, relu, yb);
-    return launched("oat_conv3d_bf16");
+        return set_error(OAT_ERR_INVALID_ARG, "oat_conv3d_bf16: need cin a multiple of 16 up to 96, cout in {16, 32, 48, 64, 96}");
+    return launch_conv3d_tc(nx, ny, nz, cin, cout, x, w, bias, relu, y, (cudaStream_t)stream);
 }
+
+int oat_unet_check(void) { return conv_tc_check(); }
 
 int oat_conv3d_flip_weights(int cin, int cout, const void *w, void *wf, void *stream) {
     if (cin < 1 || cout < 1 || !w || !wf) return set_error(OAT_ERR_INVALID_ARG, "oat_conv3d_flip_weights: bad arguments");

@@ -2,7 +2,7 @@
 
 The network maps the backprojection H^T y (scaled by its maximum) to an initial estimate x_0
 for FISTA-TV.  Convolutions run in liboat.so's tensor-core kernels (BF16 activations and
-weights, FP32 accumulation, include/oat_unet.h); training uses the library's own backward
+weights, FP32 accumulation in tensor memory, tcgen05.mma, include/oat_unet.h); training uses the library's own backward
 kernels (input gradients by the same convolution with flipped weights, weight gradients on the
 FP32 cores) and an Adam step kernel.  This module orders the calls and owns the buffers.
 """
@@ -34,6 +34,7 @@ _SIGS = {
     "oat_head_grad": [_ll, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "oat_mse": [_ll, _vp, _vp, _vp, _vp, _vp],
     "oat_adam": [_ll, _vp, _vp, _vp, _vp, _f, _f, _f, _f, _i, _vp, _vp],
+    "oat_unet_check": [],
 }
 for _n, _a in _SIGS.items():
     getattr(_lib, _n).argtypes = _a

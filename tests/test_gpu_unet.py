@@ -1,5 +1,5 @@
-"""The U-Net kernels (BF16 tensor-core convolutions, backward kernels) against the FP64
-reference (oracle/unet.py).  BF16 storage bounds the agreement: outputs are rounded to 8-bit
+"""The U-Net kernels (BF16 convolutions on the 5th-generation tensor cores, backward kernels)
+against the FP64 reference (oracle/unet.py).  BF16 storage bounds the agreement: outputs are rounded to 8-bit
 mantissas (relative 2^-9), so elementwise comparisons use 2^-8 of the reference magnitude."""
 import ctypes
 
@@ -41,6 +41,7 @@ def test_conv3d_forward_and_input_gradient(env, cin, cout, shape):
     z, yy, xx = shape
     unet._call("oat_conv3d_bf16", xx, yy, z, cin, cout, unet._p(xt), unet._p(wt), unet._p(bt), 1, unet._p(y), None)
     torch.cuda.synchronize()
+    unet._call("oat_unet_check")          # no pipeline wait of the tensor-core kernel ran out
     want = ref.conv3d(x, w, b.astype(np.float64), relu=True)
     got = y.float().cpu().numpy()
     assert np.all(np.abs(got - want) <= 2.0 ** -8 * np.abs(want) + 1e-6 * np.abs(want).max())
@@ -54,6 +55,7 @@ def test_conv3d_forward_and_input_gradient(env, cin, cout, shape):
         if cout % 16 == 0:
             unet._call("oat_conv3d_bf16", xx, yy, z, cout, cin, unet._p(gt), unet._p(wf), None, 0, unet._p(dx), None)
             torch.cuda.synchronize()
+            unet._call("oat_unet_check")
             # adjoint: <conv(x, w), g> = <x, conv^T(g)>; conv^T written out from the definition
             wflip = np.transpose(w[::-1], (0, 2, 1))
             want_dx = ref.conv3d(g, wflip)
@@ -61,6 +63,39 @@ def test_conv3d_forward_and_input_gradient(env, cin, cout, shape):
             assert np.all(np.abs(got_dx - want_dx) <= 2.0 ** -8 * np.abs(want_dx) + 1e-6 * np.abs(want_dx).max())
             lhs = (ref.conv3d(x, w) * g).sum()
             assert lhs == pytest.approx((x * want_dx).sum(), rel=1e-9)
+
+
+@pytest.mark.parametrize("shape", [(8, 16, 128), (4, 6, 200), (2, 3, 1)])
+def test_conv3d_tile_shapes(env, shape):
+    """Tiles of 128 voxels along x (one row), several tiles per row with a partial last one, and a
+    row of one voxel: the tensor-core kernel against the FP64 convolution."""
+    torch, unet = env
+    rng = np.random.default_rng(sum(shape))
+    cin, cout = 32, 48
+    x = bf16_round(rng.standard_normal(shape + (cin,)))
+    w = bf16_round(rng.standard_normal((27, cout, cin)) * 0.1)
+    xt = torch.from_numpy(x.astype(np.float32)).cuda().to(torch.bfloat16)
+    wt = torch.from_numpy(w.astype(np.float32)).cuda().to(torch.bfloat16)
+    y = torch.empty(shape + (cout,), dtype=torch.bfloat16, device="cuda")
+    z, yy, xx = shape
+    unet._call("oat_conv3d_bf16", xx, yy, z, cin, cout, unet._p(xt), unet._p(wt), None, 0, unet._p(y), None)
+    torch.cuda.synchronize()
+    unet._call("oat_unet_check")
+    want = ref.conv3d(x, w)
+    got = y.float().cpu().numpy()
+    assert np.all(np.abs(got - want) <= 2.0 ** -8 * np.abs(want) + 1e-6 * np.abs(want).max())
+
+
+def test_conv3d_rejects_unaligned(env):
+    """The TMA copies and vector stores need 16-byte alignment: refused on the host."""
+    torch, unet = env
+    from paper_1304_2017_gb300 import oat
+    x = torch.zeros(4 * 4 * 4 * 16 + 8, dtype=torch.bfloat16, device="cuda")
+    w = torch.zeros(27 * 16 * 16, dtype=torch.bfloat16, device="cuda")
+    y = torch.zeros(4 * 4 * 4 * 16, dtype=torch.bfloat16, device="cuda")
+    rc = unet._lib.oat_conv3d_bf16(4, 4, 4, 16, 16, ctypes.c_void_p(x.data_ptr() + 2), unet._p(w), None, 0,
+                                   unet._p(y), None)
+    assert rc == oat.OAT_ERR_INVALID_ARG and "aligned" in oat.oat_last_error()
 
 
 def test_weight_gradient(env):
