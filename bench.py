@@ -452,6 +452,23 @@ def run_conv(args):
     torch.cuda.synchronize()
     unet._call("oat_unet_check")
     sec = e0.elapsed_time(e1) * 1e-3 / args.steps
+    # the weight gradient of the same layer (training), on the tensor cores too
+    dw = torch.zeros(27 * cout * cin, device="cuda")
+    db = torch.zeros(cout, device="cuda")
+
+    def wcall():
+        unet._call("oat_conv3d_wgrad", n, n, n, cin, cout, unet._p(x), unet._p(y), unet._p(dw), unet._p(db),
+                   ctypes.c_void_p(s))
+    for _ in range(args.warmup):
+        wcall()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        wcall()
+    e1.record()
+    torch.cuda.synchronize()
+    unet._call("oat_unet_check")
+    wsec = e0.elapsed_time(e1) * 1e-3 / args.steps
     flop = 2.0 * 27 * cin * cout * n ** 3
     peaks, src = _peaks()
     peak = float(peaks.get("bf16_tflops", 1900.0))
@@ -459,6 +476,7 @@ def run_conv(args):
             "value": flop / sec * 1e-12, "unit": "TFLOP/s", "seconds_per_conv": sec, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": f"{n}^3 voxels, {cin} -> {cout} channels, channels last"},
+            "weight_gradient": {"seconds": wsec, "tflops": flop / wsec * 1e-12},
             "roofline": {"bound": "tensor", "achieved": flop / sec * 1e-12, "peak": peak, "unit": "TFLOP/s",
                          "frac": flop / sec * 1e-12 / peak, "peak_source": f"{src} dense BF16 burst (cuBLAS)"}}
     print(json.dumps(line), flush=True)

@@ -33,7 +33,12 @@ int oat_unet_check(void);
 int oat_conv3d_flip_weights(int cin, int cout, const void *w, void *wf, void *stream);
 
 /* dw[tap][co][ci] += sum_v g[v][co] x[v + off(tap)][ci];  db[co] += sum_v g[v][co] (db may be
- * NULL).  FP32 accumulation; cin * cout <= 6144. */
+ * NULL).  On the tensor cores (tcgen05.mma, BF16 in, FP32 accumulation in tensor memory), the
+ * voxels split over blocks whose partial sums are added in a fixed order: no floating-point atomics,
+ * the same result on every run.  cin a multiple of 16 up to 96, cout a multiple of 8 up to 128;
+ * x and g 16-byte aligned.  The partial sums live in a static device array of this library (8 MB on
+ * every GPU that loads it): weight-gradient calls whose work overlaps on the GPU (different
+ * streams) race on it; order them. */
 int oat_conv3d_wgrad(int nx, int ny, int nz, int cin, int cout, const void *x, const void *g, float *dw, float *db,
                      void *stream);
 

@@ -26,6 +26,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 #include <string>
@@ -268,6 +269,178 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
 }
 
+// ----------------------------------------------------------------------- weight gradient
+// dW[tap][co][ci] = sum_v g[v][co] x[v + off(tap)][ci] and db[co] = sum_v g[v][co] on the tensor
+// cores: per tap a GEMM with M = co (128 rows, those >= cout zero), N = ci plus one column of ones
+// (its result is the bias gradient: the voxels' g rows are zero outside the grid), K = voxels in
+// chunks of one x-run of up to 128 voxels.  Both operands are MN-major as the activations are
+// stored (8 channels contiguous per voxel): a TMA box (8 channels, bx voxels) is one column of
+// core matrices along K (8-row groups 128 bytes apart, LBO) and the 8-channel groups follow at
+// 2048 bytes (SBO).  Rows a box does not write stay zero (the buffers are cleared once), so
+// chunks shorter than the 16-voxel MMA step add nothing.  Block (tap, split) sums the chunks
+// split, split + S, ... in TMEM and writes its partial to g_wgrad_ws; k_wgrad_reduce then adds the
+// splits in a fixed order: no floating-point atomics, the same result on every run.
+constexpr int kWgStages = 3;
+constexpr int kWgSplitMax = 8;
+constexpr int kWgGroupBytes = 2048;                 // 128 voxel rows x 16 bytes
+constexpr size_t kWgWsFloats = (size_t)27 * kWgSplitMax * 96 * 97;
+__device__ float g_wgrad_ws[kWgWsFloats];         // partial dW and db of every (tap, split)
+
+struct WgArgs {
+    int nx, ny, nz, cin, cout;
+    int bx, tiles_x, splits;
+    long long nchunks;
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_wgrad_tc(const __grid_constant__ CUtensorMap mapG, const __grid_constant__ CUtensorMap mapX, WgArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full_bar[kWgStages], empty_bar[kWgStages], done_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_abort;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cin = a.cin, cout = a.cout;
+    const int tap = blockIdx.x / a.splits, split = blockIdx.x % a.splits;
+    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    const int n_groups_b = cin / 8 + 2;                       // x channels, the ones column, zeros
+    const uint32_t a_region = 16u * kWgGroupBytes, b_region = (uint32_t)n_groups_b * kWgGroupBytes;
+    const uint32_t stage_bytes = a_region + b_region;
+    const uint32_t tx_bytes = (uint32_t)(cout / 8 + cin / 8) * a.bx * 16u;
+    const int ksteps = (a.bx + 15) / 16;
+    const long long my_chunks = a.nchunks > split ? (a.nchunks - split + a.splits - 1) / a.splits : 0;
+    const uint32_t sbase = (smem_u32(smem) + 1023u) & ~1023u;
+    unsigned char *sgen = smem + (sbase - smem_u32(smem));
+
+    // clear every stage (rows no box writes must be zero) and set the ones column of B
+    for (uint32_t i = threadIdx.x * 16u; i < stage_bytes * kWgStages; i += kTcThreads * 16u)
+        *reinterpret_cast<uint4 *>(sgen + i) = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kWgStages * 128; i += kTcThreads) {
+        const int st = i / 128, v = i % 128;
+        *reinterpret_cast<unsigned short *>(sgen + st * stage_bytes + a_region + (cin / 8) * kWgGroupBytes + v * 16) =
+            (unsigned short)0x3F80;   // bf16 1.0
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the tensor cores
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < kWgStages; ++st) {
+            mbar_init(smem_u32(&full_bar[st]), 1);
+            mbar_init(smem_u32(&empty_bar[st]), 1);
+        }
+        mbar_init(smem_u32(&done_bar), 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    long long issued = 0, waited = 0;
+
+    if (threadIdx.x == 0) {
+        for (long long i = 0; i < my_chunks; ++i) {
+            const int st = (int)(i % kWgStages);
+            if (i >= kWgStages && !mbar_wait(smem_u32(&empty_bar[st]), (uint32_t)((i / kWgStages - 1) & 1))) {
+                atomicOr(&g_tc_error, 1u);
+                s_abort = 1;
+                break;
+            }
+            if (*(volatile int *)&s_abort) break;
+            const long long c = split + i * a.splits;
+            const int xt = (int)(c % a.tiles_x);
+            const long long r = c / a.tiles_x;
+            const int yy = (int)(r % a.ny), zz = (int)(r / a.ny), x0 = xt * a.bx;
+            const uint32_t bar = smem_u32(&full_bar[st]);
+            const uint32_t sa = sbase + st * stage_bytes, sb = sa + a_region;
+            mbar_expect_tx(bar, tx_bytes);
+            for (int gi = 0; gi < cout / 8; ++gi) tma_load_4d(sa + gi * kWgGroupBytes, &mapG, gi * 8, x0, yy, zz, bar);
+            for (int gi = 0; gi < cin / 8; ++gi)
+                tma_load_4d(sb + gi * kWgGroupBytes, &mapX, gi * 8, x0 + dx, yy + dy, zz + dz, bar);
+            issued = i + 1;
+        }
+    } else if (threadIdx.x == 32) {
+        // A and B MN-major (bits 15, 16), N = cin + 16
+        const uint32_t idesc = idesc_bf16(128, cin + 16) | (1u << 15) | (1u << 16);
+        for (long long i = 0; i < my_chunks; ++i) {
+            const int st = (int)(i % kWgStages);
+            if (!mbar_wait(smem_u32(&full_bar[st]), (uint32_t)((i / kWgStages) & 1))) {
+                atomicOr(&g_tc_error, 1u);
+                s_abort = 1;
+                break;
+            }
+            waited = i + 1;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = sbase + st * stage_bytes, sb = sa + a_region;
+            for (int j = 0; j < ksteps; ++j) {
+                const uint64_t da = smem_desc(sa + 256u * j, 128u, (uint32_t)kWgGroupBytes);
+                const uint64_t db = smem_desc(sb + 256u * j, 128u, (uint32_t)kWgGroupBytes);
+                mma_bf16_tc(tmem, da, db, idesc, (i > 0 || j > 0) ? 1u : 0u);
+            }
+            mma_commit(smem_u32(&empty_bar[st]));
+        }
+        mma_commit(smem_u32(&done_bar));
+    }
+    __syncwarp();
+
+    const bool ok = mbar_wait(smem_u32(&done_bar), 0u);
+    if (!ok) {
+        atomicOr(&g_tc_error, 1u);
+        s_abort = 1;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (__all_sync(0xffffffffu, ok && !*(volatile int *)&s_abort)) {
+        const int co = warp * 32 + lane;
+        float *dst = g_wgrad_ws + (((size_t)tap * a.splits + split) * cout + (co < cout ? co : 0)) * (cin + 1);
+        for (int c = 0; c < cin + 16; c += 16) {
+            float v[16];
+            if (my_chunks > 0) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);   // warp-collective
+            else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = 0.f;
+            }
+            if (co < cout) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    if (c + i <= cin) dst[c + i] = v[i];   // column cin: the bias gradient
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_abort) {
+        for (long long t = waited; t < issued; ++t)
+            mbar_wait(smem_u32(&full_bar[t % kWgStages]), (uint32_t)((t / kWgStages) & 1));
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
+    }
+}
+
+// dw[tap][co][ci] += sum_s partial[tap][s][co][ci] and db[co] += sum_s partial[13][s][co][cin], the
+// splits in order.
+__global__ void k_wgrad_reduce(int cin, int cout, int splits, float *dw, float *db) {
+    const int n = 27 * cout * cin;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int tap = i / (cout * cin), r = i % (cout * cin), co = r / cin, ci = r % cin;
+        float s = 0.f;
+        for (int k = 0; k < splits; ++k) s += g_wgrad_ws[(((size_t)tap * splits + k) * cout + co) * (cin + 1) + ci];
+        dw[i] += s;
+        if (db && tap == 13 && ci == 0) {
+            float b = 0.f;
+            for (int k = 0; k < splits; ++k) b += g_wgrad_ws[(((size_t)13 * splits + k) * cout + co) * (cin + 1) + cin];
+            db[co] += b;
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------------ host side
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -344,6 +517,58 @@ int launch_conv3d_tc(int nx, int ny, int nz, int cin, int cout, const void *x, c
     k_conv3d_tc<<<(unsigned)tiles, kTcThreads, smem, s>>>(mA, mB, a);
     e = cudaGetLastError();
     return e == cudaSuccess ? OAT_OK : set_error(OAT_ERR_CUDA, std::string("oat_conv3d_bf16: ") + cudaGetErrorString(e));
+}
+
+int launch_wgrad_tc(int nx, int ny, int nz, int cin, int cout, const void *x, const void *g, float *dw, float *db,
+                    cudaStream_t s) {
+    if (((uintptr_t)x & 15) || ((uintptr_t)g & 15))
+        return set_error(OAT_ERR_INVALID_ARG, "oat_conv3d_wgrad: x and g must be 16-byte aligned");
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return set_error(OAT_ERR_CUDA, "oat_conv3d_wgrad: cuTensorMapEncodeTiled is not available");
+    WgArgs a;
+    a.nx = nx; a.ny = ny; a.nz = nz; a.cin = cin; a.cout = cout;
+    a.bx = nx < 128 ? nx : 128;
+    a.tiles_x = (nx + a.bx - 1) / a.bx;
+    a.nchunks = (long long)a.tiles_x * ny * nz;
+    // voxel splits per tap: about one block per SM in all, within the workspace
+    int splits = current_sm_count() / 27;
+    if (splits < 1) splits = 1;
+    if (splits > kWgSplitMax) splits = kWgSplitMax;
+    while (splits > 1 && (size_t)27 * splits * cout * (cin + 1) > kWgWsFloats) --splits;
+    if ((long long)splits > a.nchunks) splits = (int)std::max(1LL, a.nchunks);
+    a.splits = splits;
+    CUtensorMap mG, mX;
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    {
+        const cuuint64_t dims[4] = {(cuuint64_t)cout, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+        const cuuint64_t strides[3] = {(cuuint64_t)cout * 2, (cuuint64_t)nx * cout * 2, (cuuint64_t)ny * nx * cout * 2};
+        const cuuint32_t box[4] = {8, (cuuint32_t)a.bx, 1, 1};
+        CUresult r = enc(&mG, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(g), dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+            return set_error(OAT_ERR_CUDA, "oat_conv3d_wgrad: tensor map of the gradient: error " + std::to_string((int)r));
+    }
+    {
+        const cuuint64_t dims[4] = {(cuuint64_t)cin, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+        const cuuint64_t strides[3] = {(cuuint64_t)cin * 2, (cuuint64_t)nx * cin * 2, (cuuint64_t)ny * nx * cin * 2};
+        const cuuint32_t box[4] = {8, (cuuint32_t)a.bx, 1, 1};
+        CUresult r = enc(&mX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(x), dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+            return set_error(OAT_ERR_CUDA, "oat_conv3d_wgrad: tensor map of the activations: error " + std::to_string((int)r));
+    }
+    const size_t smem = (size_t)kWgStages * (16 + cin / 8 + 2) * kWgGroupBytes + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_conv3d_wgrad: ") + cudaGetErrorString(e));
+    k_wgrad_tc<<<(unsigned)(27 * splits), kTcThreads, smem, s>>>(mG, mX, a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(OAT_ERR_CUDA, std::string("oat_conv3d_wgrad: ") + cudaGetErrorString(e));
+    const int n = 27 * cout * cin;
+    k_wgrad_reduce<<<(unsigned)std::min(1024, (n + 255) / 256), 256, 0, s>>>(cin, cout, splits, dw, db);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? OAT_OK : set_error(OAT_ERR_CUDA, std::string("oat_conv3d_wgrad: ") + cudaGetErrorString(e));
 }
 
 int conv_tc_check() {

@@ -151,6 +151,8 @@ int launch_fbp_kpos(Plan &p, const int *nodes, const int *qs, int n, double *out
 // tensor-core convolution of the learned warm start (conv_tc.cu)
 int launch_conv3d_tc(int nx, int ny, int nz, int cin, int cout, const void *x, const void *w, const float *bias, int relu,
                      void *y, cudaStream_t s);
+int launch_wgrad_tc(int nx, int ny, int nz, int cin, int cout, const void *x, const void *g, float *dw, float *db,
+                    cudaStream_t s);
 int conv_tc_check();
 int set_adjoint_attributes();
 int set_forward_attributes();

@@ -8,7 +8,8 @@
 // conv_tc.cu.  The input gradient of a 'same' 3x3x3 convolution is the same convolution of the
 // output gradient with the kernel flipped in space and transposed in channels, so the same kernel
 // serves the backward pass (k_flip_weights builds that kernel).
-// k_conv3d_wgrad: weight and bias gradients on the FP32 cores (training only).
+// The weight and bias gradients (oat_conv3d_wgrad) also run on the tensor cores (conv_tc.cu), with a
+// fixed-order reduction over voxel splits.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -28,63 +29,6 @@ __global__ void k_flip_weights(int cin, int cout, const bf16 *__restrict__ w, bf
         const int co = i % cout, ci = (i / cout) % cin, tap = i / (cout * cin);
         wf[i] = w[((size_t)(26 - tap) * cout + co) * cin + ci];
     }
-}
-
-// dw[tap][co][ci] += sum_v g[v][co] x[v + off(tap)][ci]; db[co] += sum_v g[v][co].
-// Block: one tap, a run of voxels, a tile of (co, ci); FP32 partial sums, one atomic each.
-constexpr int kWG = 256, kWV = 32;
-__global__ void __launch_bounds__(kWG) k_conv3d_wgrad(int nx, int ny, int nz, int cin, int cout,
-                                                       const bf16 *__restrict__ x, const bf16 *__restrict__ g,
-                                                       float *dw, float *db, int vox_per_block) {
-    extern __shared__ float sh[];
-    float *sg = sh, *sx = sh + kWV * cout;
-    const int tap = blockIdx.y;
-    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-    const long long N = (long long)nx * ny * nz;
-    const long long v0 = (long long)blockIdx.x * vox_per_block;
-    const long long v1 = min(N, v0 + vox_per_block);
-    const int pairs = cin * cout;
-    constexpr int kPer = 24;
-    float acc[kPer];
-#pragma unroll
-    for (int i = 0; i < kPer; ++i) acc[i] = 0.f;
-    float bacc = 0.f;
-    for (long long vb = v0; vb < v1; vb += kWV) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < kWV * cout; i += blockDim.x) {
-            const long long v = vb + i / cout;
-            sg[i] = v < v1 ? __bfloat162float(g[v * cout + i % cout]) : 0.f;
-        }
-        for (int i = threadIdx.x; i < kWV * cin; i += blockDim.x) {
-            const long long v = vb + i / cin;
-            float val = 0.f;
-            if (v < v1) {
-                const int xx = (int)(v % nx) + dx, yy = (int)((v / nx) % ny) + dy, zz = (int)(v / ((long long)nx * ny)) + dz;
-                if (xx >= 0 && xx < nx && yy >= 0 && yy < ny && zz >= 0 && zz < nz)
-                    val = __bfloat162float(x[(((long long)zz * ny + yy) * nx + xx) * cin + i % cin]);
-            }
-            sx[i] = val;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < kPer; ++i) {
-            const int pidx = threadIdx.x + i * kWG;
-            if (pidx < pairs) {
-                const int co = pidx / cin, ci = pidx % cin;
-                float s = acc[i];
-                for (int t = 0; t < kWV; ++t) s = fmaf(sg[t * cout + co], sx[t * cin + ci], s);
-                acc[i] = s;
-            }
-        }
-        if (tap == 13 && threadIdx.x < cout)
-            for (int t = 0; t < kWV; ++t) bacc += sg[t * cout + threadIdx.x];
-    }
-#pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-        const int pidx = threadIdx.x + i * kWG;
-        if (pidx < pairs && acc[i] != 0.f) atomicAdd(dw + (size_t)tap * pairs + pidx, acc[i]);
-    }
-    if (tap == 13 && threadIdx.x < cout && db && bacc != 0.f) atomicAdd(db + threadIdx.x, bacc);
 }
 
 // c = a + b (BF16, FP32 add)
@@ -263,14 +207,10 @@ int oat_conv3d_flip_weights(int cin, int cout, const void *w, void *wf, void *st
 
 int oat_conv3d_wgrad(int nx, int ny, int nz, int cin, int cout, const void *x, const void *g, float *dw, float *db,
                      void *stream) {
-    if (nx < 1 || ny < 1 || nz < 1 || cin < 1 || cout < 1 || cin * cout > 24 * kWG || !x || !g || !dw)
-        return set_error(OAT_ERR_INVALID_ARG, "oat_conv3d_wgrad: bad arguments (cin * cout <= 6144)");
-    const long long N = (long long)nx * ny * nz;
-    const int per = 2048;
-    const dim3 grid((unsigned)((N + per - 1) / per), 27);
-    const size_t smem = sizeof(float) * kWV * (cin + cout);
-    k_conv3d_wgrad<<<grid, kWG, smem, (cudaStream_t)stream>>>(nx, ny, nz, cin, cout, (const bf16 *)x, (const bf16 *)g, dw, db, per);
-    return launched("oat_conv3d_wgrad");
+    if (nx < 1 || ny < 1 || nz < 1 || cin < 16 || cin > 96 || cin % 16 || cout < 8 || cout > 128 || cout % 8 || !x ||
+        !g || !dw)
+        return set_error(OAT_ERR_INVALID_ARG, "oat_conv3d_wgrad: need cin a multiple of 16 up to 96, cout a multiple of 8 up to 128");
+    return launch_wgrad_tc(nx, ny, nz, cin, cout, x, g, dw, db, (cudaStream_t)stream);
 }
 
 int oat_add_bf16(long long n, const void *a, const void *b, void *c, void *stream) {

@@ -120,6 +120,37 @@ def test_weight_gradient(env):
     assert np.allclose(db.cpu().numpy(), g.sum(axis=(0, 1, 2)), rtol=1e-4, atol=1e-4)
 
 
+@pytest.mark.parametrize("shape,cin,cout", [((6, 10, 200), 32, 16), ((3, 4, 5), 96, 32), ((2, 2, 130), 16, 64)])
+def test_weight_gradient_tiles_and_determinism(env, shape, cin, cout):
+    """Weight and bias gradients on the tensor cores over several x tiles, voxel splits and channel
+    counts, against the FP64 sum; two calls give bit-identical results (fixed-order reduction)."""
+    torch, unet = env
+    rng = np.random.default_rng(sum(shape) + cin)
+    x = bf16_round(rng.standard_normal(shape + (cin,)))
+    g = bf16_round(rng.standard_normal(shape + (cout,)))
+    xt = torch.from_numpy(x.astype(np.float32)).cuda().to(torch.bfloat16)
+    gt = torch.from_numpy(g.astype(np.float32)).cuda().to(torch.bfloat16)
+    z, y, xx = shape
+    outs = []
+    for _ in range(2):
+        dw = torch.zeros(27 * cout * cin, device="cuda")
+        db = torch.zeros(cout, device="cuda")
+        unet._call("oat_conv3d_wgrad", xx, y, z, cin, cout, unet._p(xt), unet._p(gt), unet._p(dw), unet._p(db), None)
+        torch.cuda.synchronize()
+        unet._call("oat_unet_check")
+        outs.append((dw.clone(), db.clone()))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    xp = np.pad(x, ((1, 1), (1, 1), (1, 1), (0, 0)))
+    want = np.zeros((27, cout, cin))
+    for tap in range(27):
+        dz, dy, dx_ = tap // 9, (tap // 3) % 3, tap % 3
+        want[tap] = np.einsum("zyxo,zyxi->oi", g, xp[dz:dz + z, dy:dy + y, dx_:dx_ + xx])
+    got = outs[0][0].cpu().numpy().reshape(27, cout, cin)
+    scale = np.abs(want).max()
+    assert np.abs(got - want).max() <= 1e-5 * scale, np.abs(got - want).max() / scale
+    assert np.allclose(outs[0][1].cpu().numpy(), g.sum(axis=(0, 1, 2)), rtol=1e-5, atol=1e-5 * np.abs(g).sum(axis=(0, 1, 2)).max())
+
+
 def test_network_gradient_against_fp64_finite_differences(env):
     """Loss = mean (net(x) - t)^2 on an 8^3 grid: parameter gradients of the device backward
     (BF16 activations) against central differences of the FP64 reference network with the same
