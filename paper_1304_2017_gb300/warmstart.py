@@ -108,9 +108,10 @@ def evaluate(plan, net, pairs, solver, tol, max_iters):
     return rows
 
 
-def run(n_train=48, n_test=8, epochs=60, lr=2e-3, target_iters=200, tol=1e-3, max_iters=400, mu_rel=1e-6, n=64):
+def run(n_train=48, n_test=8, epochs=60, lr=2e-3, target_iters=200, tol=1e-3, max_iters=400, mu_rel=1e-6, n=64,
+        samples=384):
     torch.cuda.set_device(0)
-    geom = geometry(n=n)
+    geom = geometry(n=n, samples=samples)
     plan = oat.Plan(geom)
     solver = FistaTV(plan, mu=0.0, inner=5)
     L = solver.lipschitz(iters=40)
