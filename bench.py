@@ -87,7 +87,9 @@ def _counters():
         return {}
     if c.get("_kernel_source_hash") != kernel_source_hash():
         return {}
-    return {k: v for k, v in c.items() if not k.startswith("_")}
+    out = {k: v for k, v in c.items() if not k.startswith("_")}
+    out["source"] = c.get("_about")
+    return out
 
 
 def l2_read_gbs(dev, mb=48, reps=100):
@@ -250,6 +252,38 @@ def run_reference(args):
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def pls_small(dev):
+    """The metric's third part on a workload that fits the default run: PLS-TV (FISTA-TV, x >= 0,
+    5 FGP iterations, mu = 1e-6 L) from zero to a 1e-3 relative data residual, noise-free data
+    u = H alpha of a seeded ellipsoid/sphere phantom, on the 64^3 @ 0.25 mm grid with 32 rings x
+    45 views (1440 transducers) on 50 mm and K = 384; GPU seconds by CUDA events (the step-size
+    estimate, 40 power iterations, reported apart)."""
+    import torch
+    from paper_1304_2017_gb300 import oat, warmstart
+    from paper_1304_2017_gb300.fista import FistaTV
+    geom = warmstart.geometry(n=64)
+    plan = oat.Plan(geom, device=dev.index or 0)
+    alpha = torch.from_numpy(warmstart.phantom(geom, 20_000)).to(dev)
+    u = plan.project(alpha).clone()
+    solver = FistaTV(plan, mu=0.0, inner=5)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    L = solver.lipschitz(iters=40)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    solver.mu = 1e-6 * L
+    _, info = solver.solve(u, iters=400, tol=1e-3)
+    r = info["residual"]
+    k = next((i for i, v in enumerate(r) if v <= 1e-3), None)
+    plan.close()
+    return {"value": info["gpu_seconds"][k] if k is not None else None, "unit": "s", "higher_is_better": False,
+            "metric": "PLS-TV GPU seconds to a 1e-3 relative data residual (zero start)",
+            "iterations": (k + 1) if k is not None else None, "final_residual": r[-1],
+            "step_size_estimate_s": e0.elapsed_time(e1) * 1e-3, "mu": solver.mu,
+            "workload": "64^3 @ 0.25 mm, 32 rings x 45 views (1440 transducers) on 50 mm, K=384 @ 20 MHz, c=1.5, "
+                        "noise-free, held-out phantom seed 20000"}
 
 
 def run_pls(args):
@@ -482,16 +516,21 @@ def run_conv(args):
     print(json.dumps(line), flush=True)
 
 
-def run_capture():
-    """The workload restricted to 64 transducers (rings 10, 30, 50, 64, 70, 90, 110, 120 x views
-    0, 20, ..., 140): 2.9e9 interpolations per operator, ~2 GB on the device."""
+def run_capture(n_xdcr=64):
+    """The workload restricted to a few transducers, for ncu captures: 64 (rings 10, 30, 50, 64,
+    70, 90, 110, 120 x views 0, 20, ..., 140; 2.9e9 interpolations per operator, ~2 GB on the
+    device) or 256 (16 rings x 16 views spread over the scan), H and H^T twice."""
     import torch
 
     from paper_1304_2017_gb300 import oat
     from paper_1304_2017_gb300 import workloads as W
     torch.cuda.set_device(0)
     g = W.config("c2")
-    qs = [r * 180 + v for r in (10, 30, 50, 64, 70, 90, 110, 120) for v in range(0, 160, 20)]
+    if n_xdcr == 64:
+        qs = [r * 180 + v for r in (10, 30, 50, 64, 70, 90, 110, 120) for v in range(0, 160, 20)]
+    else:
+        side = int(round(n_xdcr ** 0.5))
+        qs = [int(r) * 180 + int(v) for r in np.linspace(4, 123, side).round() for v in np.linspace(0, 179, side).round()]
     sub = g.subset(qs)
     plan = oat.Plan(sub)
     alpha = torch.from_numpy(W.phantom("c2", g)).cuda()
@@ -511,6 +550,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-pls", action="store_true", help="skip the small PLS-TV figure of the default line")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--learned", action="store_true",
                     help="learned warm start: train the U-Net on PLS-TV targets, compare time to a 1e-3 residual")
@@ -530,13 +570,14 @@ def main():
     ap.add_argument("--conv", action="store_true",
                     help="one tensor-core 3x3x3 convolution of the U-Net (64 -> 64 channels) on a --conv-size^3 grid")
     ap.add_argument("--conv-size", type=int, default=128)
+    ap.add_argument("--capture-transducers", type=int, default=64, help="transducers of --capture (64 or a square)")
     ap.add_argument("--capture", action="store_true",
                     help="small case for ncu captures: the 256^3 workload on 64 transducers, H and H^T twice")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.capture:
-        return run_capture()
+        return run_capture(args.capture_transducers)
     if args.conv:
         return run_conv(args)
     if args.learned:
@@ -639,27 +680,30 @@ def main():
     n_sm = _sm_count(dev)
     peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = FLOP_PER_SAMPLE * pts / (dom_ms * 1e-3) / 1e12
-    counters = _counters().get(dom_name.split()[0], {})
+    allc = _counters()
+    counters = dict(allc.get(dom_name.split()[0], {}))
+    counters["source"] = allc.get("source")
     traffic = counters.get("dram_bytes_per_launch")
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": achieved / peak_tflops, "traffic": traffic, "kernel": dom_name,
             "kernel_ms": dom_ms, "peak_source": f"{src} clock: {n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
             "flop_per_sample": FLOP_PER_SAMPLE}
-    # on-chip bounds of the dominant kernel: instruction issue (4 warp instructions per clock per
-    # SM) at its measured instruction count, and L2 bytes against a measured L2 copy bandwidth
+    # on-chip utilisation of the dominant kernel, measured by ncu on the 64-transducer capture case
+    # (profiles/counters.json, valid only for the profiled kernel sources): the fraction of issue
+    # slots used and of the shared-memory pipe's one wavefront per SM clock, with the shared
+    # wavefronts per sample that the second applies to
     onchip = {}
-    ips = counters.get("warp_instructions_per_sample")
-    if ips:
-        bound = n_sm * 4 * sm_max * 1e6 / ips
-        onchip["issue"] = {"warp_instructions_per_sample": ips, "bound_samples_per_s": bound,
-                           "achieved_samples_per_s": pts / (dom_ms * 1e-3), "frac": pts / (dom_ms * 1e-3) / bound}
+    for key in ("issue_active_pct", "shared_pipe_pct", "shared_wavefronts_per_sample",
+                "warp_instructions_per_sample"):
+        if counters.get(key) is not None:
+            onchip[key] = counters[key]
     l2_peak = l2_read_gbs(dev)
     lts = counters.get("lts_bytes_per_launch")
     onchip["l2"] = {"peak_gbs": l2_peak, "peak_source": "measured here: oat_probe_read over a 48 MB L2-resident buffer",
                     "achieved_gbs": (lts / (dom_ms * 1e-3) / 1e9) if lts else None}
     if lts:
         onchip["l2"]["frac"] = onchip["l2"]["achieved_gbs"] / l2_peak
-    onchip["counters_source"] = "profiles/counters.json (ncu, one pass at full size; instructions from the --set full capture)"
+    onchip["counters_source"] = counters.get("source", "none valid for these kernel sources")
 
     variant = (", exact strip-area lattice weights" if args.lattice_weights else "") + \
               (f", {args.eir} transducer response (H = H^e D G)" if args.eir else "")
@@ -674,6 +718,11 @@ def main():
             "kernel_ms": {"k_brick_gather": g_ms / max(g_n, 1), "k_brick_gather_t": b_ms / max(b_n, 1)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
             "roofline": roof, "onchip": onchip, "clocks": clocks}
+    if rank == 0 and not args.no_pls:
+        try:
+            line["pls_tv"] = pls_small(dev)
+        except Exception as exc:  # the PLS-TV figure must not hide the operator line
+            line["pls_tv"] = {"value": None, "note": f"failed: {exc}"}
     if rank == 0 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline(geom, alpha_np, y_np, n_xdcr=int(os.environ.get("OAT_CPU_XDCR", "16")))
