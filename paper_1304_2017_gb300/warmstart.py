@@ -36,16 +36,21 @@ def phantom(geom, seed):
     return W.ellipsoids_phantom(geom, n=int(rng.integers(8, 24)), seed=seed, semi_range=(0.4, 2.5), a_range=(0.2, 1.0))
 
 
-def make_pairs(plan, geom, seeds, solver, target_iters):
+def make_pairs(plan, geom, seeds, solver, target_iters, with_target=True):
+    """Data, network input and (for training pairs) the PLS-TV target of each seeded phantom;
+    held-out pairs need no target (with_target=False)."""
     pairs = []
     for s in seeds:
         alpha = torch.from_numpy(phantom(geom, s)).cuda()
         u = plan.project(alpha).clone()
         bp = plan.backproject(u).clone()
-        x, info = solver.solve(u, iters=target_iters)
         scale = 1.0 / max(float(bp.abs().max()), 1e-30)
-        pairs.append({"seed": s, "u": u, "bp": bp, "scale": scale, "target": (x * scale).clone(), "alpha": alpha,
-                      "target_residual": info["residual"][-1]})
+        p = {"seed": s, "u": u, "bp": bp, "scale": scale, "alpha": alpha}
+        if with_target:
+            x, info = solver.solve(u, iters=target_iters)
+            p["target"] = (x * scale).clone()
+            p["target_residual"] = info["residual"][-1]
+        pairs.append(p)
     return pairs
 
 
@@ -118,7 +123,7 @@ def run(n_train=48, n_test=8, epochs=60, lr=2e-3, target_iters=200, tol=1e-3, ma
     solver.mu = mu_rel * L
     t0 = time.time()
     train_pairs = make_pairs(plan, geom, range(10_000, 10_000 + n_train), solver, target_iters)
-    test_pairs = make_pairs(plan, geom, range(20_000, 20_000 + n_test), solver, target_iters)
+    test_pairs = make_pairs(plan, geom, range(20_000, 20_000 + n_test), solver, target_iters, with_target=False)
     t_data = time.time() - t0
     net = UNet(geom.vol_shape, seed=3)
     t0 = time.time()
