@@ -26,8 +26,7 @@
 // is chosen from the largest M_q and the plan's bound on the contributions one node can
 // receive, so that no 64-bit sum can overflow.
 // k_finish_t        alpha'_n = sum_n 2^-e_g Delta_s^2 as float32: every voxel written once.
-// AREA instances scale each point's g' by its ring's exact-strip-area weight factor (carried
-// in a per-warp queue beside the points).  With a transducer response set, eir.cu's k_eir_t
+// AREA instances scale each point's g' by its ring's exact-strip-area weight factor.  With a transducer response set, eir.cu's k_eir_t
 // first forms z = H^e^T y and the gather reads z as float32 data.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -139,8 +138,6 @@ struct NodeLayout {
     static constexpr int NN2 = 2 * NN + ((2 * NN) & 3 ? 4 - ((2 * NN) & 3) : 0);
 };
 
-constexpr int kQueue = 64;   // per-warp queue of owned points (power of two, >= 63)
-
 // Scatter one owned point (cell-local weights wx, wy, wz; first node b in the low 16 bits of
 // e.w, the point's shell s within the unit above them) with value wg[s].
 // The eight weights are the products (g uz_or_wz) uy_or_wy ux_or_wx in that order, formed in
@@ -171,14 +168,12 @@ __device__ __forceinline__ void scatter8(int *shi, unsigned int *slo, float4 e, 
 
 template <int B, int DT, bool AREA>
 __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
-    extern __shared__ int shi[];   // node-sum high halves, low halves, segment slots, queues, views
+    extern __shared__ int shi[];   // node-sum high halves, low halves, segment slots, views
     using NL = NodeLayout<B>;
     constexpr int S1 = NL::S1, S2 = NL::S2, NN = NL::NN, NN2 = NL::NN2;
     unsigned int *slo = (unsigned int *)(shi + NN);
     SegSlot *slots = (SegSlot *)(shi + NN2);
-    float4 *queues = (float4 *)(slots + kAdjThreads);
-    BrickView *views = (BrickView *)(queues + kQueue * (kAdjThreads / 32));
-    float *wqueues = (float *)(views + kAdjThreads / 32);   // ring weights of queued points (AREA)
+    BrickView *views = (BrickView *)(slots + kAdjThreads);
     const int nqc = (a.Q + a.qchunk - 1) / a.qchunk;
     const int brick = blockIdx.x / nqc;
     const int q0 = (blockIdx.x % nqc) * a.qchunk;
@@ -209,11 +204,8 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
     __shared__ struct { float scale; int qe; long long fold; } s_pass;   // the current pass: unit, end
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     SegSlot *ws = slots + warp * 32;
-    float4 *wq = queues + warp * kQueue;
-    float *wrq = wqueues + warp * kQueue;
     __shared__ float s_wg[kAdjThreads / 32][kShells];
     float *wg = s_wg[warp];
-    const unsigned lt_mask = (1u << lane) - 1u;
 
     int qe = q0;   // end of the current pass, read from s_pass right after the pass's first barrier
     for (int qp = q0; qp < q1; qp = qe) {
@@ -304,7 +296,6 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
             __syncwarp();
             if (lane < kShells) wg[lane] = gs;   // g' of the unit's shells, read by scatter8
             __syncwarp();
-            int qh = 0, qt = 0;   // queue head and tail (warp-uniform)
             for (int ib = 0; ib < T; ib += 32) {
                 int shell;
                 const int gidx = unit_ring(ib + lane, T, p0, p1, p2, gbase, shell);
@@ -327,28 +318,13 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
                                   (unsigned)lc[2] < (unsigned)E[2];
                             ent = make_float4(w[0], w[1], w[2], __int_as_float((lc[2] * S2 + lc[1] * S1 + lc[0]) | (sh << 16)));
                         }
-                        // queue the owned points; scatter them 32 at a time with every lane busy
-                        const unsigned om = __ballot_sync(0xffffffffu, own);
-                        if (own) {
-                            const int slot = (qt + __popc(om & lt_mask)) & (kQueue - 1);
-                            wq[slot] = ent;
-                            if (AREA) wrq[slot] = wr;
-                        }
-                        qt += __popc(om);
-                        __syncwarp();
-                        if (qt - qh >= 32) {
-                            const int slot = (qh + lane) & (kQueue - 1);
-                            scatter8<S1, S2>(shi, slo, wq[slot], wg, AREA ? wrq[slot] : 1.f);
-                            qh += 32;
-                            __syncwarp();
-                        }
+                        // each lane scatters its own point (about 93 % of the candidates are
+                        // owned; a per-warp queue that kept every lane of the scatter busy cost
+                        // more in its shared stores, loads and bookkeeping: measured 10 % slower)
+                        if (own) scatter8<S1, S2>(shi, slo, ent, wg, AREA ? wr : 1.f);
                     }
                     __syncwarp();
                 }
-            }
-            if (lane < qt - qh) {
-                const int slot = (qh + lane) & (kQueue - 1);
-                scatter8<S1, S2>(shi, slo, wq[slot], wg, AREA ? wrq[slot] : 1.f);
             }
             __syncwarp();
         }
@@ -491,9 +467,8 @@ int launch_backproject_static(Plan &p, const void *data, float *vol, cudaStream_
 }
 
 size_t adjoint_smem_bytes(bool area) {
-    return sizeof(int) * NodeLayout<kBA>::NN2 + sizeof(SegSlot) * kAdjThreads +
-           sizeof(float4) * kQueue * (kAdjThreads / 32) + sizeof(BrickView) * (kAdjThreads / 32) +
-           (area ? sizeof(float) * kQueue * (kAdjThreads / 32) : 0);
+    (void)area;
+    return sizeof(int) * NodeLayout<kBA>::NN2 + sizeof(SegSlot) * kAdjThreads + sizeof(BrickView) * (kAdjThreads / 32);
 }
 
 int set_adjoint_attributes() {
