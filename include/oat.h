@@ -176,6 +176,9 @@ int oat_backproject_noalloc(oat_plan plan, const void *d_data, float *d_vol, voi
  *                                   + [p_{q,k} + (k~ - k)(p_{q,k+1} - p_{q,k})] / (k~ + t_min/dt) },
  *   k~ = (|r_q - r_n| / c - t_min) / dt, k = floor(k~)
  * (the same sum as the paper's Eq. disfbp), samples outside 0 .. K-1 counting as zero.
+ * The sum is discontinuous where k~ crosses an integer; the kernel reads the pair k, k + 1 of the
+ * exact k~: k~ is formed in FP32 (good to about 2e-6 grid units of distance) and recomputed in
+ * double precision wherever it lies within 1e-5 (ds / (c dt) + 1) samples of an integer.
  *
  * oat_plan_set_fbp_weights: w_q, one per transducer (host array of n_transducers doubles; for a
  *   spherical scan, the patch area over the sphere radius, R^s dtheta dphi sin theta_q).  Copied

@@ -25,7 +25,9 @@ int oat_probe_read(const void *d_buf, long long n_bytes, int reps, float *d_sink
 /*
  * The fractional sample index k~ = (|r_q - r_n| / c - t_min) / dt of Eqs. linearint and disfbp
  * (Sec. III.C) exactly as oat_fbp computes it in FP32 (from its brick-centre distance in float
- * pairs plus the node's FP32 offset), for n (node, transducer) pairs:
+ * pairs plus the node's FP32 offset), for n (node, transducer) pairs.  This is the estimate
+ * before oat_fbp's double-precision resolution of values within its guard band of an integer:
+ * its error against the definition must stay well inside that band.
  *   d_nodes        device, int [n][3]: (ix, iy, iz) node indices (any integers: only arithmetic)
  *   d_transducers  device, int [n]: transducer indices
  *   d_out          device, double [n]: k~ as oat_fbp holds it (integer part plus FP32 fraction,

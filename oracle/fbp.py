@@ -54,15 +54,11 @@ def sample_positions(geom, nodes, transducers):
     return (d / geom.c_mm_per_us - geom.t_min_us) / (1.0 / geom.fs_mhz)
 
 
-def fbp(geom, p, weights, nodes=None, absolute=False, ambiguity=0.0):
+def fbp(geom, p, weights, nodes=None, absolute=False):
     """alpha_fbp from data p [Q][K] (Eq. disfbp): on the whole node grid of `geom` as
     (nz, ny, nx), or at the nodes given as (ix, iy, iz) triples (a 1-D array).
 
-    absolute=True sums the terms' magnitudes instead (the scale of the sum's rounding).
-    ambiguity=eps > 0 returns (alpha, amb) with amb_n the total change of node n's terms when
-    every k~ within eps of an integer r is read on the other side of it (k = r - 1 instead of
-    k = r, or back): Eq. disfbp is discontinuous there (its difference moves to the next sample
-    pair), so an evaluation whose k~ is good to eps may take either value."""
+    absolute=True sums the terms' magnitudes instead (the scale of the sum's rounding)."""
     p = np.asarray(p, np.float64).reshape(geom.data_shape)
     w = np.asarray(weights, np.float64).reshape(geom.n_transducers)
     dt = 1.0 / geom.fs_mhz
@@ -76,7 +72,6 @@ def fbp(geom, p, weights, nodes=None, absolute=False, ambiguity=0.0):
         nd = np.asarray(nodes, np.int64).reshape(-1, 3)
         X, Y, Z = xs[nd[:, 0]], ys[nd[:, 1]], zs[nd[:, 2]]
     acc = np.zeros(X.shape)
-    amb = np.zeros(X.shape)
 
     def term(q, k, kt):
         def sample(j):
@@ -93,12 +88,5 @@ def fbp(geom, p, weights, nodes=None, absolute=False, ambiguity=0.0):
         k = np.floor(kt).astype(np.int64)
         t = term(q, k, kt)
         acc += np.abs(t) if absolute else t
-        if ambiguity > 0.0:
-            r = np.rint(kt).astype(np.int64)
-            near = np.abs(kt - r) < ambiguity
-            if near.any():
-                alt = np.where(k == r, r - 1, r)                 # the other side of the integer
-                amb += np.where(near, np.abs(term(q, alt, kt) - t), 0.0)
     scale = 1.0 / (math.pi * geom.gruneisen * c * dt)
-    alpha = (1.0 if absolute else -1.0) * acc * scale
-    return (alpha, amb * scale) if ambiguity > 0.0 else alpha
+    return (1.0 if absolute else -1.0) * acc * scale

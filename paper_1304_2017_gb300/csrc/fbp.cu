@@ -18,6 +18,13 @@
 //        (the braces of Eq. disfbp rewritten), summed with compensation over a tile and in
 //        double across tiles; every voxel is written once.  Tiles whose sample windows lie
 //        inside the record (the usual case) skip the per-sample bounds tests.
+//        Eq. disfbp is discontinuous where k~ crosses an integer (the sample pair k, k + 1
+//        changes), so the pair must be the one the exact k~ selects.  Where the FP32 weight
+//        w = k~ - k is within a guard band of 0 or 1 -- g = 1e-5 (ds / (c dt) + 1) samples, at
+//        least four times the FP32 error bound of k~ -- the pair and the weight are taken from
+//        k~ recomputed in double precision from the node index and the transducer position (the
+//        definition of Eq. linearint).  Outside the band the FP32 floor equals the exact one.
+//        The band holds about 2g of the pairs (1e-4 at the 256^3 / 65 mm scan).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -44,6 +51,8 @@ struct FbpArgs {
     float t0_hi, t0_lo;          // t_min / dt as a float pair
     int R, W;                    // staged sample windows: offset R, width W = 2 R + 1
     double scale;                // -1 / (pi Gamma c dt)
+    double sk64, t0_64;          // ds / (c dt) and t_min / dt in double (exact sample positions)
+    float guard;                 // half-width of the band around integers resolved in double
 };
 
 // Per (brick, transducer): unit vector u, distance D (index units), integer and fractional part
@@ -138,6 +147,34 @@ __device__ __forceinline__ void fbp_kpos(const FbpQ &Q, float dx, float dy, f32x
     KF = fma2(DDD, pk2(sk, sk), pk2(Q.kfrac, Q.kfrac));
 }
 
+// Sample position k~ - kint of node (ix, iy, iz) for transducer q in double precision: the
+// distance from the node to the transducer (index units, T = hi + lo exactly) times ds / (c dt),
+// minus t_min / dt (Eq. linearint).  Called only for pairs in the guard band.
+__device__ __noinline__ double fbp_kexact(const float4 *__restrict__ xd, double sk64, double t0_64, int q, int ix,
+                                          int iy, int iz, int kint) {
+    const float4 hi = __ldg(xd + 2 * q), lo = __ldg(xd + 2 * q + 1);
+    const double vx = (double)ix - ((double)hi.x + (double)lo.x);
+    const double vy = (double)iy - ((double)hi.y + (double)lo.y);
+    const double vz = (double)iz - ((double)hi.z + (double)lo.z);
+    const double d = sqrt(fma(vx, vx, fma(vy, vy, vz * vz)));
+    return fma(d, sk64, -t0_64) - (double)kint;
+}
+
+// Replaces the floor fk and the weight w = k~ - fk of a pair in the guard band by those of the
+// exact sample position.
+// The exact floor differs from the FP32 one by at most one inside the band; anything else (a
+// transducer the set-up marked as contributing nothing, a non-finite position) keeps the FP32
+// values, whose sample indices are known to lie in the kernel's window.
+__device__ __forceinline__ void fbp_resolve(const FbpArgs &a, int q, int ix, int iy, int iz, int kint, float &fk,
+                                            float &w) {
+    const double ke = fbp_kexact(a.xd, a.sk64, a.t0_64, q, ix, iy, iz, kint);
+    const double fe = floor(ke);
+    if (fabs(fe - (double)fk) <= 1.0) {
+        fk = (float)fe;
+        w = (float)(ke - fe);
+    }
+}
+
 // The (voxel, transducer) terms of two voxels at offsets (dx, dy, dz0|1) from the brick centre
 // (packed DZ, DD): w_q {..} of Eq. disfbp for each, packed.  Per voxel the
 // operations and their rounding are those of the one-voxel form: distance change dD, sample
@@ -145,19 +182,35 @@ __device__ __forceinline__ void fbp_kpos(const FbpQ &Q, float dx, float dy, f32x
 // count as zero (else every sample read is known to be inside).  STAGED: row is the brick's
 // window of this transducer's samples in shared memory, sample kint - R + j at j (zero outside
 // the record), so that sample k reads row[k - kint + R].
+// A voxel whose k~ lies in the guard band takes its pair and weight from fbp_resolve
+// (transducer q; the voxels are nodes (ix, iy, iz0) and (ix, iy, iz0 + 4)).
 template <int MODE, typename T>
-__device__ __forceinline__ f32x2 fbp_pair(const FbpQ &Q, const T *row, int K, float dx, float dy, f32x2 DZ, f32x2 DD,
-                                          float sk, int R) {
+__device__ __forceinline__ f32x2 fbp_pair(const FbpArgs &a, int q, int ix, int iy, int iz0, const FbpQ &Q,
+                                          const T *row, int K, float dx, float dy, f32x2 DZ, f32x2 DD, float sk,
+                                          int R) {
     constexpr bool CHECK = MODE == 1, STAGED = MODE == 2;
     f32x2 DDD, KF;
     fbp_kpos(Q, dx, dy, DZ, DD, sk, DDD, KF);
     const f32x2 SK = pk2(sk, sk);
     float kfa, kfb;
     upk2(KF, kfa, kfb);
-    const float fka = floorf(kfa), fkb = floorf(kfb);
-    const int ka = (STAGED ? R : Q.kint) + int_of_integral(fka), kb = (STAGED ? R : Q.kint) + int_of_integral(fkb);
+    float fka = floorf(kfa), fkb = floorf(kfb);
     const f32x2 M1 = pk2(-1.f, -1.f);
-    const f32x2 WGT = fma2(pk2(fka, fkb), M1, KF);                 // k~ - k
+    f32x2 WGT = fma2(pk2(fka, fkb), M1, KF);                       // k~ - k
+    {
+        // |w - 1/2| > 1/2 - g: the weight is within g of 0 or 1, k~ within g of an integer
+        float ua, ub;
+        upk2(add2(WGT, pk2(-0.5f, -0.5f)), ua, ub);
+        const float lim = 0.5f - a.guard;
+        if ((fabsf(ua) > lim || fabsf(ub) > lim) && Q.w != 0.f) {
+            float wa, wb;
+            upk2(WGT, wa, wb);
+            if (fabsf(ua) > lim) fbp_resolve(a, q, ix, iy, iz0, Q.kint, fka, wa);
+            if (fabsf(ub) > lim) fbp_resolve(a, q, ix, iy, iz0 + 4, Q.kint, fkb, wb);
+            WGT = pk2(wa, wb);
+        }
+    }
+    const int ka = (STAGED ? R : Q.kint) + int_of_integral(fka), kb = (STAGED ? R : Q.kint) + int_of_integral(fkb);
     const f32x2 TAU = fma2(DDD, SK, pk2(Q.tau, Q.tau));
     float p0a, p1a, p0b, p1b;
     if (CHECK) {
@@ -233,11 +286,13 @@ __global__ void __launch_bounds__(kFbpThreads) k_fbp(FbpArgs a) {
     }
         if (STAGED) {
             for (int t = 0; t < nt; ++t)
-                OAT_FBP_ACC((fbp_pair<2>(tq[t], swin + t * a.W, a.K, dx, dy, DZ, DD, sk, a.R)))
+                OAT_FBP_ACC((fbp_pair<2>(a, q0 + t, ix, iy, iz, tq[t], swin + t * a.W, a.K, dx, dy, DZ, DD, sk, a.R)))
         } else if (all_inside) {
-            for (int t = 0; t < nt; ++t, row += a.K) OAT_FBP_ACC((fbp_pair<0>(tq[t], row, a.K, dx, dy, DZ, DD, sk, 0)))
+            for (int t = 0; t < nt; ++t, row += a.K)
+                OAT_FBP_ACC((fbp_pair<0>(a, q0 + t, ix, iy, iz, tq[t], row, a.K, dx, dy, DZ, DD, sk, 0)))
         } else {
-            for (int t = 0; t < nt; ++t, row += a.K) OAT_FBP_ACC((fbp_pair<1>(tq[t], row, a.K, dx, dy, DZ, DD, sk, 0)))
+            for (int t = 0; t < nt; ++t, row += a.K)
+                OAT_FBP_ACC((fbp_pair<1>(a, q0 + t, ix, iy, iz, tq[t], row, a.K, dx, dy, DZ, DD, sk, 0)))
         }
 #undef OAT_FBP_ACC
         float s0, s1, c0, c1;
@@ -273,6 +328,11 @@ __global__ void k_fbp_kpos(FbpArgs a, const int *__restrict__ nodes, const int *
     out[i] = (double)Q.kint + (double)kf;
 }
 
+// Half-width of the guard band in samples for sk = ds / (c dt) samples per grid unit: 1e-5 grid
+// units of distance plus 1e-5 samples, at least four times the FP32 error of k~ (measured at most
+// 2.2e-6 grid units of distance, FP32 rounding of the fraction included).
+static double fbp_guard(double sk) { return 1e-5 * (sk + 1.0); }
+
 static void fbp_args(const Plan &p, FbpArgs &a) {
     a.xd = p.d_fbp;
     a.nx = p.nx; a.ny = p.ny; a.nz = p.nz; a.K = p.K; a.Q = p.Q;
@@ -281,6 +341,8 @@ static void fbp_args(const Plan &p, FbpArgs &a) {
     a.sk_hi = (float)sk; a.sk_lo = (float)(sk - (double)a.sk_hi);
     a.t0_hi = (float)t0; a.t0_lo = (float)(t0 - (double)a.t0_hi);
     a.scale = -1.0 / (M_PI * p.g.gruneisen * p.g.c_mm_per_us * p.dt);
+    a.sk64 = sk; a.t0_64 = t0;
+    a.guard = (float)fbp_guard(sk);
 }
 
 int launch_fbp_kpos(Plan &p, const int *nodes, const int *qs, int n, double *out, cudaStream_t s) {

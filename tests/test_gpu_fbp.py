@@ -1,21 +1,19 @@
 """Parity of the sm_103a filtered backprojection (oat_fbp, through the C ABI) with the FP64
 reference oracle/fbp.py (Eq. disfbp).
 
-Tolerance 1e-5 relative L2: per term the kernel keeps the sample position to about 1e-6 of a
-sample (float-pair distance to each brick centre, small FP32 offsets) and sums with
-compensation, so its error stays near FP32 rounding of the data and weights.  FP16 / BF16 data
-are read exactly, so the reference gets the same rounded values.
+Tolerance 1e-5 relative L2, on the raw difference: per term the kernel keeps the sample position
+to about 1e-6 of a sample (float-pair distance to each brick centre, small FP32 offsets) and sums
+with compensation, so its error stays near FP32 rounding of the data and weights.  FP16 / BF16
+data are read exactly, so the reference gets the same rounded values.
 
 Eq. disfbp is discontinuous in the sample position: where k~ crosses an integer the one-sided
-difference p_{k+1} - p_k moves to the next pair, so a rounding difference that moves k~ across
-an integer changes that term by the second difference of the data.  The kernel's k~ error is
-measured directly (oat_fbp_sample_positions against the FP64 definition, `kt_max`); where the
-exact k~ lies within twice that error bound of a sample both sides are readings the FP32 kernel may
-take, so the comparison allows each node the reference's total change over such pairs
-(`ambiguity`) and holds everything else to the tolerance.  The raw error is printed beside it.
-The data are band-limited, as measured pressure is (Gaussian pulses several samples wide, or the
-forward model's data of an object): for white noise the second difference is as large as the
-data."""
+difference p_{k+1} - p_k moves to the next pair.  The kernel therefore recomputes k~ in double
+precision wherever its FP32 value lies within a guard band of an integer (half-width
+g = 1e-5 (ds / (c dt) + 1) samples), so that it reads the pair the exact k~ selects.  The FP32
+error of k~ is measured directly (oat_fbp_sample_positions against the FP64 definition) and must
+stay below a quarter of g, which is what makes the band sufficient.  The forward-model cases
+(smooth blobs and uniform spheres, whose pulses have sharp edges) are the ones with crossings
+that move a node visibly."""
 import numpy as np
 import pytest
 
@@ -41,27 +39,11 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def rel_beyond(got, want, amb):
-    """Relative L2 of the part of got - want that the integer-crossing allowance amb does not
-    explain."""
-    d = np.maximum(np.abs(np.asarray(got, np.float64) - want) - amb, 0.0)
-    return float(np.linalg.norm(d) / np.linalg.norm(want))
-
-
-# The kernel's k~ error is a distance error: measured by test_fbp_sample_position_accuracy on
-# every small case and on sampled pairs of the 256^3 / 23,040-transducer scan at 1.1e-6 to 1.9e-6
-# grid units at most (rms 2.5e-7), bounded here by KT_GRID grid units, i.e. KT_GRID ds / (c dt)
-# samples.  The window of the integer-crossing allowance is twice that bound.
-KT_GRID = 2.2e-6
-
-
-def kt_max(geom):
-    """Bound of the kernel's k~ error in samples for this geometry."""
-    return KT_GRID * geom.spacing_mm * geom.fs_mhz / geom.c_mm_per_us
-
-
-def eps_k(geom):
-    return 2.0 * kt_max(geom)
+# Half-width of the kernel's guard band in samples (fbp.cu, fbp_guard): 1e-5 grid units of
+# distance plus 1e-5 samples.
+def guard(geom):
+    sk = geom.spacing_mm * geom.fs_mhz / geom.c_mm_per_us
+    return 1e-5 * (sk + 1.0)
 
 
 def smooth_data(geom, seed, width=6.0, n_pulses=3):
@@ -93,6 +75,10 @@ def blob_phantom(geom, seed, n=3, sigma_vox=2.5):
 def _data(geom, kind, seed):
     if kind == "smooth":
         return smooth_data(geom, seed)
+    if kind == "noise":
+        # white N(0,1) data: the second difference at a crossing is as large as the data, so a
+        # pair read on the wrong side of an integer would show at once
+        return np.random.default_rng(seed).standard_normal(geom.data_shape).astype(np.float32)
     import oracle
     if kind == "spheres":
         # the forward model's own data (the oracle, FP64) of uniform spheres: sharp edges, so large
@@ -111,6 +97,7 @@ CASES = {
     "window_cut": (lambda: W.make_geometry(14, 0.31, 3, 4, 8.11, 30), "smooth"),
     "physical": (lambda: W.make_geometry(20, 0.251, 6, 8, 8.03, 160), "forward"),
     "physical_spheres": (lambda: W.make_geometry(20, 0.251, 6, 8, 8.03, 160), "spheres"),
+    "physical_noise": (lambda: W.make_geometry(20, 0.251, 6, 8, 8.03, 160), "noise"),
     # coarse grid at 40 MHz: about 16 samples per grid spacing, so a brick's sample windows are
     # too wide to stage in shared memory and the kernel reads the data directly
     "coarse_direct": (lambda: W.make_geometry(10, 0.61, 3, 4, 9.13, 400, fs_mhz=40.0), "smooth"),
@@ -123,7 +110,8 @@ def test_fbp_matches_reference(env, case, dtype):
     torch, oat = env
     make, kind = CASES[case]
     geom = make()
-    n_r = {"ragged": 3, "tmin0": 2, "window_cut": 3, "physical": 6, "physical_spheres": 6, "coarse_direct": 3}[case]
+    n_r = {"ragged": 3, "tmin0": 2, "window_cut": 3, "physical": 6, "physical_spheres": 6, "physical_noise": 6,
+           "coarse_direct": 3}[case]
     n_v = geom.n_transducers // n_r
     w = F.arc_weights(geom.positions_mm, n_r, n_v)
     p = _data(geom, kind, 11)
@@ -131,11 +119,10 @@ def test_fbp_matches_reference(env, case, dtype):
     plan.set_fbp_weights(w)
     pt = torch.from_numpy(p).cuda().to(plan.torch_data_dtype)
     got = plan.fbp(pt).cpu().numpy()
-    want, amb = F.fbp(geom, pt.float().cpu().numpy(), w, ambiguity=eps_k(geom))
+    want = F.fbp(geom, pt.float().cpu().numpy(), w)
     assert np.abs(want).max() > 0
-    print(f"fbp {case} dtype {dtype}: raw rel-L2 {rel(got, want):.3e}, beyond the allowance "
-          f"{rel_beyond(got, want, amb):.3e}")
-    assert rel_beyond(got, want, amb) <= TOL, (rel(got, want), rel_beyond(got, want, amb))
+    print(f"fbp {case} dtype {dtype}: rel-L2 {rel(got, want):.3e}")
+    assert rel(got, want) <= TOL, rel(got, want)
     plan.close()
 
 
@@ -149,10 +136,11 @@ def _kt_errors(oat, geom, nodes, qs):
 
 @pytest.mark.parametrize("case", sorted(CASES) + ["c2_sampled"])
 def test_fbp_sample_position_accuracy(env, case):
-    """The kernel's own k~ (oat_fbp_sample_positions runs the arithmetic of k_fbp) against the
+    """The kernel's FP32 k~ (oat_fbp_sample_positions runs the arithmetic of k_fbp) against the
     FP64 definition: every (node, transducer) pair of the small cases, 400,000 sampled pairs of
     the 256^3 / 23,040-transducer scan (distances up to about 450 grid units).  The largest error
-    bounds the integer-crossing window used by the parity tests (twice the bound)."""
+    must stay below a quarter of the guard band in which the kernel resolves k~ in double
+    precision, so that outside the band its FP32 floor is the exact one."""
     torch, oat = env
     if case == "c2_sampled":
         geom = W.config("c2")
@@ -169,9 +157,9 @@ def test_fbp_sample_position_accuracy(env, case):
     err = _kt_errors(oat, geom, nodes, qs)
     sk = geom.spacing_mm * geom.fs_mhz / geom.c_mm_per_us
     print(f"fbp k~ error {case}: max {err.max():.3e} samples ({err.max() / sk:.3e} grid units), "
-          f"rms {np.sqrt((err ** 2).mean()):.3e} samples over {len(err)} pairs; bound {kt_max(geom):.3e}")
+          f"rms {np.sqrt((err ** 2).mean()):.3e} samples over {len(err)} pairs; guard band {guard(geom):.3e}")
     assert np.isfinite(err).all()
-    assert err.max() <= kt_max(geom), (err.max(), kt_max(geom))
+    assert err.max() <= 0.25 * guard(geom), (err.max(), guard(geom))
 
 
 def test_fbp_full_size_sampled_nodes(env):
@@ -187,11 +175,47 @@ def test_fbp_full_size_sampled_nodes(env):
     rng = np.random.default_rng(5)
     nodes = rng.integers(0, 256, size=(64, 3))
     nodes[:8, 0] = 0; nodes[8:16, 1] = 255; nodes[16:24, 2] = 0
-    want, amb = F.fbp(geom, p, w, nodes=nodes, ambiguity=eps_k(geom))
+    want = F.fbp(geom, p, w, nodes=nodes)
     got_s = got[nodes[:, 2], nodes[:, 1], nodes[:, 0]]
-    print(f"fbp full size: raw rel-L2 {rel(got_s, want):.3e}, beyond the allowance {rel_beyond(got_s, want, amb):.3e}")
-    assert rel_beyond(got_s, want, amb) <= TOL, (rel(got_s, want), rel_beyond(got_s, want, amb))
+    print(f"fbp full size: rel-L2 {rel(got_s, want):.3e}")
+    assert rel(got_s, want) <= TOL, rel(got_s, want)
     plan.close()
+
+
+@pytest.mark.parametrize("offset", [-5e-6, -1e-6, 1e-6, 5e-6])
+def test_fbp_constructed_crossing(env, offset):
+    """A crossing placed on purpose: the time origin puts node 0 at k~ = n + offset samples for
+    transducer 0 (inside the kernel's guard band, and for |offset| <= 5e-6 within reach of the
+    FP32 error of k~), under a sharp pulse whose second difference there is large.  The kernel
+    must read the pair the exact k~ selects: node 0 and the whole volume against the reference."""
+    import dataclasses
+    torch, oat = env
+    g0 = W.make_geometry(16, 0.27, 4, 6, 7.3, 200)
+    dt = 1.0 / g0.fs_mhz
+    xs, ys, zs = g0.node_coords_mm()
+    d = np.linalg.norm(np.array([xs[0], ys[0], zs[0]]) - g0.positions_mm[0])
+    kt = (d / g0.c_mm_per_us - g0.t_min_us) / dt
+    g = dataclasses.replace(g0)
+    g.t_min_us = g0.t_min_us + (kt - np.floor(kt) - offset) * dt
+    kt1 = F.sample_positions(g, [[0, 0, 0]], [0])[0]
+    assert abs(kt1 - np.rint(kt1) - offset) < 1e-9, kt1
+    t = g.t_min_us + np.arange(g.n_samples) * dt
+    p = (np.exp(-0.5 * ((t[None, :] - d / g.c_mm_per_us) / (1.2 * dt)) ** 2)
+         * np.linspace(0.5, 1.0, g.n_transducers)[:, None]).astype(np.float32)
+    w = F.arc_weights(g.positions_mm, 4, 6)
+    plan = oat.Plan(g)
+    plan.set_fbp_weights(w)
+    got = plan.fbp(torch.from_numpy(p).cuda()).cpu().numpy()
+    plan.close()
+    want = F.fbp(g, p, w)
+    # the term of transducer 0 at node 0 on the other side of the integer, for scale
+    wrong = dataclasses.replace(g)
+    wrong.t_min_us = g.t_min_us + 2.0 * offset * dt
+    alt = F.fbp(wrong, p, w)
+    assert abs(alt[0, 0, 0] - want[0, 0, 0]) > 1e-3 * np.abs(want).max()       # a real crossing
+    e0 = abs(got[0, 0, 0] - want[0, 0, 0]) / np.abs(want).max()
+    print(f"fbp crossing at {offset:+.0e}: node 0 error {e0:.2e}, volume rel-L2 {rel(got, want):.3e}")
+    assert e0 <= 1e-5 and rel(got, want) <= TOL, (e0, rel(got, want))
 
 
 def test_fbp_requires_weights(env):
