@@ -202,6 +202,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
     __syncthreads();
     const float &rb = rbs[0], &rb2 = rbs[1];
     __shared__ struct { float scale; int qe; long long fold; } s_pass;   // the current pass: unit, end
+    __shared__ int s_next;   // next unit of the pass to take (the first nwarps by the warps' indices)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     SegSlot *ws = slots + warp * 32;
     __shared__ float s_wg[kAdjThreads / 32][kShells];
@@ -255,6 +256,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
                 s_pass.scale = ldexpf(1.f, ep);
                 s_pass.fold = eg - ep < 63 ? (1LL << (eg - ep)) : 0;   // a larger shift meets only zero sums
                 s_pass.qe = qp + cut;
+                s_next = nwarps;
             }
         }
         __syncthreads();
@@ -264,7 +266,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_brick_gather_t(AdjArgs a) {
         int vq = -1;
         BrickView &v = views[warp];   // the current transducer's view of the brick (shared, per warp)
         float ex[3], ey[3];
-        for (int u = warp; u < units; u += nwarps) {
+        for (int u = warp; u < units; u = next_unit(&s_next, lane)) {
             const int q = qp + u / nkg;
             if (q != vq) {
                 __syncwarp();

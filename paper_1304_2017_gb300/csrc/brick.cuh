@@ -62,7 +62,7 @@ __device__ __forceinline__ void brick_view(const Xdcr &x, const float O[3], cons
 __device__ __forceinline__ bool shell_ring_range(const BrickView &v, float Rk, int nr, float rb2, int &ilo, int &ihi) {
     if (nr <= 1) return false;
     const float dd = Rk - v.d;
-    const float s2 = (rb2 - dd * dd) / (4.f * Rk * v.d);   // sin^2(gamma / 2)
+    const float s2 = __fdividef(rb2 - dd * dd, 4.f * Rk * v.d);   // sin^2(gamma / 2)
     if (!(s2 > 0.f)) return false;
     const float gam = s2 >= 1.f ? 3.14159265f : 2.f * asinf(sqrtf(s2));
     ilo = max(1, (int)ceilf(Rk * (v.thc - gam) - 0.01f));
@@ -91,7 +91,8 @@ __device__ __forceinline__ float acos_window(float x) {
 // which the ring's coordinate d = C_d + a m_d cos(phi - psi_d) lies in [lo_d, hi_d] (two arcs
 // per axis from two arccosines; their hull inside the window keeps the window one interval).
 // Margins of 1e-3 grid units and 2e-3 rad keep it conservative (the arccosines come from
-// acos_window); candidates are then tested exactly with their cells.
+// acos_window, the reciprocals from the approximate division, 2 ulp); candidates are then tested
+// exactly with their cells.
 __device__ __forceinline__ bool ring_box_ranges(const BrickView &v, const Ring &r, float3 C, float rb2,
                                                 const float lo[3], const float hi[3], int &a0, int &a1, int &b0,
                                                 int &b1) {
@@ -116,7 +117,7 @@ __device__ __forceinline__ bool ring_box_ranges(const BrickView &v, const Ring &
             if (Cd[d] < lo[d] - M - 1e-3f || Cd[d] > hi[d] + M + 1e-3f) return false;
             continue;
         }
-        const float inv = 1.f / M;
+        const float inv = __fdividef(1.f, M);
         const float cl = (lo[d] - 1e-3f - Cd[d]) * inv, ch = (hi[d] + 1e-3f - Cd[d]) * inv;
         if (ch < -1.f || cl > 1.f) return false;
         if (cl <= -1.f && ch >= 1.f) continue;
@@ -140,7 +141,7 @@ __device__ __forceinline__ bool ring_box_ranges(const BrickView &v, const Ring &
     if (w1 - w0 >= kTwoPiF - 1e-6f) { a1 = r.nj - 1; return true; }
     const float sh = kTwoPiF * floorf(w0 * (1.f / kTwoPiF));
     w0 -= sh; w1 -= sh;   // w0 in [0, 2 pi)
-    const float inv = 1.f / r.dphi;
+    const float inv = __fdividef(1.f, r.dphi);
     a0 = max(0, (int)ceilf(w0 * inv));
     a1 = min(r.nj - 1, (int)floorf(w1 * inv));
     if (w1 >= kTwoPiF) {
@@ -311,6 +312,15 @@ __device__ __forceinline__ int segment_point(const SegSlot *ws, int f, int lane,
     w[0] = __fsub_rn(R.x, fx); w[1] = __fsub_rn(R.y, fy); w[2] = __fsub_rn(R.z, fz);
     wr = sl.w;
     return (mp >> 6) & 3;
+}
+
+// Next unit of a warp: the warps of a block take units from a shared counter, so that a warp
+// that finishes its units early takes more (the units' sizes differ by an order of magnitude
+// between the edge and the middle of a brick's shell range).  Warp-collective.
+__device__ __forceinline__ int next_unit(int *counter, int lane) {
+    int u = 0;
+    if (lane == 0) u = atomicAdd(counter, 1);
+    return __shfl_sync(0xffffffffu, u, 0);
 }
 
 // Lowest cell L and cell counts E (<= bs) of brick id in a grid of nb[3] bricks (x fastest)

@@ -131,6 +131,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_brick_gather(FwdArgs a) {
 
     // brick centre c, cell box [blo, bhi) and bounding-sphere radius rb: block-shared constants
     __shared__ float c[3], blo[3], bhi[3], rbs[2];
+    __shared__ int s_next;   // next unit to take (the first nwarps are taken by the warps' indices)
+    if (threadIdx.x == 0) s_next = blockDim.x >> 5;
     if (threadIdx.x < 3) {
         const int d = threadIdx.x;
         c[d] = L[d] + 0.5f * E[d];
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_brick_gather(FwdArgs a) {
     __syncthreads();
     const float &rb = rbs[0], &rb2 = rbs[1];
     const double scale = COUNT ? 1.0 : pow2_scale(a.bound_pts * (double)__uint_as_float(*a.amax), 61);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long owned = 0;   // COUNT mode
     SegSlot *ws = slots + warp * 32;
     const int nkg = (a.kspan + kShells - 1) / kShells;
@@ -153,7 +155,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_brick_gather(FwdArgs a) {
     BrickView &v = views[warp];   // the current transducer's view of the brick (shared, per warp)
     float ex[3], ey[3];
 
-    for (int u = warp; u < units; u += nwarps) {
+    for (int u = warp; u < units; u = next_unit(&s_next, lane)) {
         const int q = q0 + u / nkg;
         if (q != vq) {
             __syncwarp();

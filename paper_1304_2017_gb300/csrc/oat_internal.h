@@ -248,7 +248,7 @@ __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
 // (xa, ya): the anchor's local coordinates (hi parts).  The rotation delta = m dphi (|delta| <=
 // 1 by the choice of the anchor spacing) enters through sin(delta) and cos(delta) - 1 from their
 // Taylor series through delta^11 and delta^12 (the first omitted terms are below 2e-10), Horner
-// form in FP32, the two series side by side in packed FP32 pairs.  Then
+// form in FP32 (scalar FMAs, whose coefficients are instruction immediates).  Then
 //   dx = x_A (cos delta - 1) - y_A sin delta,  dy = y_A (cos delta - 1) + x_A sin delta,
 //   P - I = f + dx e_x + dy e_y.
 __device__ __forceinline__ float3 anchor_offset(const float f[3], float xa, float ya, const float ex[3],
@@ -256,15 +256,11 @@ __device__ __forceinline__ float3 anchor_offset(const float f[3], float xa, floa
     const float mf = __int2float_rn(m);
     const float d = fmaf(mf, dphi_lo, __fmul_rn(mf, dphi));
     const float d2 = __fmul_rn(d, d);
-    const f32x2 D2 = pk2(d2, d2);
-    // (sin series, cos series): coefficients of delta^11 / delta^12 down to delta^3 / delta^4
-    f32x2 P = fma2(D2, pk2((float)(-1.0 / 39916800.0), (float)(1.0 / 479001600.0)),
-                   pk2((float)(1.0 / 362880.0), (float)(-1.0 / 3628800.0)));
-    P = fma2(D2, P, pk2((float)(-1.0 / 5040.0), (float)(1.0 / 40320.0)));
-    P = fma2(D2, P, pk2((float)(1.0 / 120.0), (float)(-1.0 / 720.0)));
-    P = fma2(D2, P, pk2((float)(-1.0 / 6.0), (float)(1.0 / 24.0)));
-    float ps, pc;
-    upk2(P, ps, pc);
+    // sin series (coefficients of delta^11 down to delta^3) and cos series (delta^12 .. delta^4)
+    const float ps = fmaf(d2, fmaf(d2, fmaf(d2, fmaf(d2, (float)(-1.0 / 39916800.0), (float)(1.0 / 362880.0)),
+                                        (float)(-1.0 / 5040.0)), (float)(1.0 / 120.0)), (float)(-1.0 / 6.0));
+    const float pc = fmaf(d2, fmaf(d2, fmaf(d2, fmaf(d2, (float)(1.0 / 479001600.0), (float)(-1.0 / 3628800.0)),
+                                        (float)(1.0 / 40320.0)), (float)(-1.0 / 720.0)), (float)(1.0 / 24.0));
     const float sd = fmaf(__fmul_rn(d, d2), ps, d);
     const float cm = __fmul_rn(d2, fmaf(d2, pc, -0.5f));
     // (dx, dy) = (xa cm - ya sd, ya cm + xa sd)
