@@ -163,8 +163,9 @@ __device__ __noinline__ double fbp_kexact(const float4 *__restrict__ xd, double 
 // Replaces the floor fk and the weight w = k~ - fk of a pair in the guard band by those of the
 // exact sample position.
 // The exact floor differs from the FP32 one by at most one inside the band; anything else (a
-// transducer the set-up marked as contributing nothing, a non-finite position) keeps the FP32
-// values, whose sample indices are known to lie in the kernel's window.
+// transducer the set-up marked as contributing nothing -- its weight is zero and its FP32 values
+// are placeholders --, a non-finite position) keeps the FP32 values, whose sample indices are
+// known to lie in the kernel's window.
 __device__ __forceinline__ void fbp_resolve(const FbpArgs &a, int q, int ix, int iy, int iz, int kint, float &fk,
                                             float &w) {
     const double ke = fbp_kexact(a.xd, a.sk64, a.t0_64, q, ix, iy, iz, kint);
@@ -202,7 +203,7 @@ __device__ __forceinline__ f32x2 fbp_pair(const FbpArgs &a, int q, int ix, int i
         float ua, ub;
         upk2(add2(WGT, pk2(-0.5f, -0.5f)), ua, ub);
         const float lim = 0.5f - a.guard;
-        if ((fabsf(ua) > lim || fabsf(ub) > lim) && Q.w != 0.f) {
+        if (fmaxf(fabsf(ua), fabsf(ub)) > lim) {
             float wa, wb;
             upk2(WGT, wa, wb);
             if (fabsf(ua) > lim) fbp_resolve(a, q, ix, iy, iz0, Q.kint, fka, wa);
