@@ -128,12 +128,14 @@ __device__ __forceinline__ void sadd(int *hi, unsigned int *lo, int idx, float x
 
 // Node layout of the brick's (B+1)^3 node sums: x stride 1, y stride S1, z stride S2, with S2
 // padded so that the 32 lanes' scatters, which follow rings in arbitrary directions, spread
-// over the banks (simulated on lattice-point warps of the 256^3 workload: 3.1 bank wavefronts
-// per atomic instead of 3.5 unpadded).
+// over the banks.  Simulated on lattice-point warps of the 256^3 workload (the same address in
+// several lanes counts as a conflict, as the measured wavefronts per atomic, 3.2, show): about
+// 3.1-3.2 bank wavefronts per atomic with the padding against 3.5 without; among paddings that
+// simulate alike, 19 (S2 = 644 at B = 24) timed 0.5 % faster than 13.
 template <int B>
 struct NodeLayout {
     static constexpr int S1 = B + 1;
-    static constexpr int S2 = S1 * (B + 1) + 13;
+    static constexpr int S2 = S1 * (B + 1) + 19;
     static constexpr int NN = S2 * (B + 1);
     static constexpr int NN2 = 2 * NN + ((2 * NN) & 3 ? 4 - ((2 * NN) & 3) : 0);
 };
