@@ -7,7 +7,9 @@
 // exact pairs), tau = d / c likewise, and f tau as a pair product whose integer part is dropped
 // exactly: the fraction keeps ~1e-10 cycle whatever the distance.  Consecutive frequencies then
 // differ by the rotation z = exp(-+j 2 pi df tau) (from sincospif, ~1 ulp), applied with one
-// complex multiply per term; every run of rotations starts from a directly evaluated phase.
+// complex multiply per term (the forward takes two of its three steps per run by the three-term
+// recurrence E_{k+1} = 2 cos(theta) E_k - E_{k-1} instead); every run of rotations starts from a
+// directly evaluated phase.
 //
 // k_sph_fwd  one warp per (transducer, run of 256 frequencies, slab of voxels), 8 consecutive
 //            frequencies per lane; the warp walks its slab 32 voxels at a time: lane j forms voxel
@@ -158,19 +160,27 @@ __global__ void __launch_bounds__(kSphFwdThreads, 3) k_sph_fwd(SphArgs a) {
             __sincosf(kTwoPi * pfrac(ph, pl), &s, &c);
             const float er0 = vw * c, ei0 = -vw * s;                 // w exp(-j 2 pi f_l0 tau)
             const float er4 = fmaf(er0, v4r, -ei0 * v4i), ei4 = fmaf(er0, v4i, ei0 * v4r);   // ... f_l0+4
-            // frequencies k and k + 4 side by side: one packed rotation serves both
-            f32x2 Er = pk2(er0, er4), Ei = pk2(ei0, ei4);
+            // frequencies k and k + 4 side by side.  E_1 = E_0 z by one packed complex rotation;
+            // then E_{k+1} = 2 cos(theta) E_k - E_{k-1} (z = exp(-j theta), so E_{k+1} + E_{k-1} =
+            // (z + 1/z) E_k), two scalar FMAs with a negated addend per step and component: half
+            // the FMA-pipe work of a complex rotation, on a pipe that bounds this kernel.  Over
+            // two steps its rounding stays within a few ulp of |E|.
+            static_assert(kSphF / 2 == 4, "E_0 .. E_3 below");
+            const f32x2 Er = pk2(er0, er4), Ei = pk2(ei0, ei4);
             const f32x2 Zr = pk2(vzr, vzr), Zi = pk2(vzi, vzi), NZi = pk2(-vzi, -vzi);
-#pragma unroll
-            for (int k = 0; k < kSphF / 2; ++k) {
-                T2r[k] = add2(T2r[k], Er);
-                T2i[k] = add2(T2i[k], Ei);
-                if (k + 1 < kSphF / 2) {
-                    const f32x2 nr = fma2(Er, Zr, mul2(Ei, NZi));
-                    Ei = fma2(Er, Zi, mul2(Ei, Zr));
-                    Er = nr;
-                }
-            }
+            T2r[0] = add2(T2r[0], Er); T2i[0] = add2(T2i[0], Ei);
+            const f32x2 E1r = fma2(Er, Zr, mul2(Ei, NZi));
+            const f32x2 E1i = fma2(Er, Zi, mul2(Ei, Zr));
+            T2r[1] = add2(T2r[1], E1r); T2i[1] = add2(T2i[1], E1i);
+            const float c2 = 2.f * vzr;
+            float a0r, a4r, a0i, a4i, b0r, b4r, b0i, b4i;
+            upk2(Er, a0r, a4r); upk2(Ei, a0i, a4i); upk2(E1r, b0r, b4r); upk2(E1i, b0i, b4i);
+            const float c0r = fmaf(c2, b0r, -a0r), c4r = fmaf(c2, b4r, -a4r);
+            const float c0i = fmaf(c2, b0i, -a0i), c4i = fmaf(c2, b4i, -a4i);
+            T2r[2] = add2(T2r[2], pk2(c0r, c4r)); T2i[2] = add2(T2i[2], pk2(c0i, c4i));
+            const float d0r = fmaf(c2, c0r, -b0r), d4r = fmaf(c2, c4r, -b4r);
+            const float d0i = fmaf(c2, c0i, -b0i), d4i = fmaf(c2, c4i, -b4i);
+            T2r[3] = add2(T2r[3], pk2(d0r, d4r)); T2i[3] = add2(T2i[3], pk2(d0i, d4i));
         }
         if ((chunk & 3) == 3 || base + 32 >= v1) {
 #pragma unroll
